@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the Steiner-tree hot path on GB300.
+
+One step = one query through the whole path (Voronoi cells, predecessor and
+bridge scan, pair compaction, MST, expansion, sorted tree and total) on the
+plain high-diameter workload: a 4096 x 4096 4-connected grid with weights
+uniform in [1, 1000] and 256 seeds drawn uniformly over the grid.  Inputs
+(graph and seed set) are seeded and synthetic.
+
+Printed (rank 0, one JSON line):
+  value      trees/s from device time (CUDA events on the library's stream,
+             graph resident in HBM), summed over ranks (replicas: each rank
+             runs its own queries)
+  e2e        trees/s through the C ABI with host seed lists in and host tree
+             edges out (copies inside the timed region)
+  roofline   the Voronoi SSSP kernel's algorithmic bytes per launch / its
+             event-timed duration, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle timed on the host cores (rank 0, N = 1)
+
+``--impl reference`` times the CPU oracle itself on the same workload.
+Multi-GPU: ``torchrun --nproc-per-node N bench.py --gpus N``; ranks are
+independent replicas (queries never exchange data), barrier + max-over-ranks
+timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 2            # the 4096^2 grid, 256 seeds
+PROFILE = os.path.join(ROOT, "profiles", "sssp_grid4096_k256.md")
+SSSP_SOURCES = ["paper_2205_14503_gb300/csrc/voronoi.cu", "paper_2205_14503_gb300/csrc/common.cuh",
+                "paper_2205_14503_gb300/csrc/internal.h"]
+
+
+def sssp_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in SSSP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per SSSP launch from the committed ncu summary, or None
+    if the summary is absent or the kernel source changed since."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m1 = re.search(r"sssp_source_hash:\s*([0-9a-f]+)", text)
+    m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    if not m1 or not m2 or m1.group(1) != sssp_source_hash():
+        return None
+    return int(m2.group(1))
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[3:7]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(rank: int):
+    import paper_2205_14503_gb300.workloads as wl
+    g = wl.config_graph(WORKLOAD)
+    (seeds,) = wl.config_seed_sets(WORKLOAD, g)
+    if rank > 0:    # replicas run their own queries of the same size
+        seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), seeds.size,
+                                   0x5EED + WORKLOAD + 1000 * rank)
+    return g, seeds
+
+
+def cpu_oracle_time(g, seeds, budget_s: float = 30.0):
+    """Time the oracle on whole queries until ~budget_s of CPU work."""
+    import oracle
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.steiner(g, seeds, want_labels=False)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all + times[-1] > budget_s or len(times) >= 3:
+            break
+    return r, times
+
+
+def config_dict(g, seeds):
+    return {"workload": "grid4096_k256", "graph": "4096x4096 4-connected grid, w~U[1,1000]",
+            "n": int(g.n), "arcs": int(g.n_arcs), "k": int(seeds.size),
+            "l2": "inputs larger than L2 (adjacency 537 MB, labels 134 MB)"}
+
+
+METRIC = "Steiner trees/s (Voronoi SSSP + bridge scan + MST + expansion)"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    g, seeds = workload(0)
+    import oracle
+    for _ in range(args.warmup):
+        oracle.steiner(g, seeds, want_labels=False)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.steiner(g, seeds, want_labels=False)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_dict(g, seeds),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "trees/s", "cores": 1,
+                             "sample": "whole queries of the workload, single-threaded C oracle"},
+            "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_14503_gb300 import steiner as st
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    g, seeds = workload(rank)
+    t0 = time.perf_counter()
+    G = st.SteinerGraph(g, device=local)
+    load_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 3)):
+        r = G.query_detail(seeds, pairs=False)
+        if r.status != st.STEINER_OK:
+            raise SystemExit(f"warm-up query failed: {st.STATUS_NAMES[r.status]} {st.last_error()}")
+
+    # device-timed pass (graph and seed set resident; per-phase CUDA events)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    phase = {k: [] for k in ("ms_init", "ms_voronoi", "ms_bridges", "ms_mst", "ms_tree")}
+    launches = 0
+    stats = None
+    for _ in range(args.steps):
+        r = G.query_detail(seeds, pairs=False)
+        stats = r.stats
+        for k in phase:
+            phase[k].append(stats[k])
+        launches += stats["gpu_launches"]
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    dev_ms = [sum(phase[k][i] for k in phase) for i in range(args.steps)]
+    dev_s = max_over_ranks(sum(dev_ms) / 1e3, world)
+
+    # end-to-end pass through the C ABI: host seeds in, host edges out
+    barrier(world)
+    torch.cuda.synchronize()
+    lat = []
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = G.query(seeds)
+        lat.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t_start, world)
+    barrier(world)
+    G.close()
+
+    if rank != 0:
+        return
+    total_q = args.steps * world
+    value = total_q / dev_s
+    n, m_arcs = g.n, g.n_arcs
+    sssp_ms = statistics.mean(phase["ms_voronoi"])
+    alg_bytes = 16 * m_arcs + 12 * n          # per SSSP launch (one query)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (sssp_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_dict(g, seeds),
+        "roofline": {"kernel": "sssp_kernel (Voronoi near/far SSSP)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                     "launch_ms": sssp_ms},
+        "e2e": {"value": total_q / e2e_s, "unit": "trees/s",
+                "h2d_bytes_per_step": int(seeds.size * 4),
+                "d2h_bytes_per_step": int(res.edges.shape[0] * 12 + 8),
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99))},
+        "gpu_launches": launches,
+        "gteps": (g.n_arcs // 2) / (sssp_ms / 1e3) / 1e9,
+        "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
+        "sssp": {"iterations": stats["iterations"], "phases": stats["phases"],
+                 "relax_attempts": stats["relax_attempts"],
+                 "work_efficiency": stats["relax_attempts"] / m_arcs,
+                 "delta": G.get_param("delta") if G.handle else None},
+        "tree": {"edges": int(res.edges.shape[0]), "total": int(res.total)},
+        "graph_load_s": load_s,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        ref, times = cpu_oracle_time(g, seeds)
+        same = bool(ref.total == res.total and np.array_equal(ref.edges, res.edges))
+        line["cpu_baseline"] = {"kind": "oracle", "value": len(times) / sum(times),
+                                "unit": "trees/s", "cores": 1,
+                                "sample": f"{len(times)} whole queries of the workload, "
+                                          "single-threaded C oracle",
+                                "matches_gpu": same}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,566 @@
+// C ABI of the library (declared in include/steiner.h): graph upload,
+// per-query device workspace, the single-query driver (Algorithm 2 end to
+// end on one stream), the Voronoi export, and the batch/serving entries.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/steiner.h"
+#include "internal.h"
+#include "engine.h"
+
+using namespace stn;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return STEINER_ECUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T *&p, uint64_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)&p, count * sizeof(T));
+}
+
+uint32_t bits_for(uint32_t n) {
+    uint32_t b = 1;
+    while (b < 32 && (1ull << b) < (uint64_t)n) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct steiner_graph {
+    int device = 0;
+    DevGraph g;
+    Geometry geo;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    Workspace ws;
+    bool ws_ready = false;
+    uint32_t nbits = 1;
+    uint32_t delta = 0;
+    uint32_t max_iters = 1u << 22;
+    Control *h_ctl = nullptr;      // pinned
+    cudaEvent_t ev[6] = {};
+    BatchEngine *batch = nullptr;
+    ServeEngine *serve = nullptr;
+};
+
+namespace {
+
+int ensure_n_workspace(steiner_graph *G) {
+    Workspace &ws = G->ws;
+    if (G->ws_ready) return STEINER_OK;
+    uint32_t n = G->g.n;
+    ws.n = n;
+    CK(dalloc(ws.label, n));
+    CK(dalloc(ws.pred_arc, n));
+    CK(dalloc(ws.stamp_near, n));
+    CK(dalloc(ws.stamp_far, n));
+    CK(dalloc(ws.mark, n));
+    CK(dalloc(ws.q[0], n));
+    CK(dalloc(ws.q[1], n));
+    CK(dalloc(ws.hq[0], G->g.heavy_chunk_cap));
+    CK(dalloc(ws.hq[1], G->g.heavy_chunk_cap));
+    CK(dalloc(ws.far[0], n));
+    CK(dalloc(ws.far[1], n));
+    CK(dalloc(ws.ctl, 1));
+    uint64_t tcap = std::max<uint64_t>(n, 2);
+    CK(dalloc(ws.tree_key, tcap));
+    CK(dalloc(ws.tree_key2, tcap));
+    CK(dalloc(ws.tree_w, tcap));
+    CK(dalloc(ws.tree_w2, tcap));
+    ws.tree_cap = (uint32_t)tcap;
+    CK(cudaMemsetAsync(ws.stamp_near, 0, (size_t)n * 4, G->stream));
+    CK(cudaMemsetAsync(ws.stamp_far, 0, (size_t)n * 4, G->stream));
+    CK(cudaMemsetAsync(ws.mark, 0, (size_t)n * 4, G->stream));
+    ws.epoch_near = ws.epoch_far = ws.epoch_mark = 1;
+    G->ws_ready = true;
+    return STEINER_OK;
+}
+
+int ensure_k_workspace(steiner_graph *G, uint32_t k) {
+    Workspace &ws = G->ws;
+    if (k > ws.seeds_cap) {
+        CK(dalloc(ws.seeds, k));
+        ws.seeds_cap = k;
+    }
+    uint64_t slots = k > 1 ? (uint64_t)k * (k - 1) / 2 : 0;
+    if (slots > (1ull << 28))
+        return fail(STEINER_ENOMEM, "seed set too large for the pair table (k(k-1)/2 > 2^28)");
+    if (slots > ws.pairtab_cap) {
+        CK(dalloc(ws.pairtab, slots));
+        ws.pairtab_cap = slots;
+    }
+    uint64_t ecap = std::min<uint64_t>(slots, G->g.m / 2 + 1);
+    if (ecap > ws.e_cap) {
+        CK(dalloc(ws.e_key, ecap));
+        CK(dalloc(ws.e_ra, ecap));
+        CK(dalloc(ws.e_rb, ecap));
+        CK(dalloc(ws.e_arc, ecap));
+        CK(dalloc(ws.e_mst, ecap));
+        ws.e_cap = ecap;
+    }
+    uint64_t tiles = std::max<uint64_t>((slots + 2047) / 2048, 64 * 256);
+    if (tiles > ws.tile_cap) {
+        CK(dalloc(ws.tile_off, tiles));
+        ws.tile_cap = (uint32_t)tiles;
+    }
+    if (k > ws.comp_cap) {
+        CK(dalloc(ws.comp, k));
+        CK(dalloc(ws.hook, k));
+        CK(dalloc(ws.best, k));
+        ws.comp_cap = k;
+    }
+    return STEINER_OK;
+}
+
+int sorted_seed_list(const steiner_graph *G, const int32_t *seeds, uint32_t k,
+                     std::vector<int32_t> &out) {
+    if (k == 0) return fail(STEINER_EINVAL, "empty seed set");
+    if (!seeds) return fail(STEINER_EINVAL, "null seed pointer");
+    out.assign(seeds, seeds + k);
+    std::sort(out.begin(), out.end());
+    for (uint32_t i = 0; i < k; ++i) {
+        if (out[i] < 0 || (uint32_t)out[i] >= G->g.n)
+            return fail(STEINER_EINVAL, "seed id out of range");
+        if (i && out[i] == out[i - 1]) return fail(STEINER_EINVAL, "duplicate seed id");
+    }
+    return STEINER_OK;
+}
+
+int status_from(const Control &c, uint32_t k, bool tree) {
+    if (c.err & (ERR_BARRIER | ERR_TIMEOUT))
+        return fail(STEINER_ETIMEOUT, "device loop or barrier hit its cap");
+    if (c.err & ERR_OVERFLOW)
+        return fail(STEINER_EOVERFLOW, "a distance or bridge sum reached 2^32 - 1");
+    if (c.err & ERR_CAPACITY) return fail(STEINER_ENOMEM, "internal buffer capacity exceeded");
+    if (tree && k > 1 && c.n_mst + 1 < k)
+        return fail(STEINER_EDISCONNECTED, "seeds lie in more than one component");
+    return STEINER_OK;
+}
+
+void advance_epochs(Workspace &ws, const Control &c, cudaStream_t s) {
+    ws.epoch_near += c.iterations + 2;
+    ws.epoch_far += c.phases + 2;
+    ws.epoch_mark += 1;
+    if (c.err != 0 || ws.epoch_near > 0x7FFFFFFFu || ws.epoch_far > 0x7FFFFFFFu || ws.epoch_mark > 0x7FFFFFFFu) {
+        cudaMemsetAsync(ws.stamp_near, 0, (size_t)ws.n * 4, s);
+        cudaMemsetAsync(ws.stamp_far, 0, (size_t)ws.n * 4, s);
+        cudaMemsetAsync(ws.mark, 0, (size_t)ws.n * 4, s);
+        ws.epoch_near = ws.epoch_far = ws.epoch_mark = 1;
+    }
+}
+
+// Runs Steps 1 (and, with `full`, 2-7) of Algorithm 2 for one sorted seed
+// list.  Leaves the control block in G->h_ctl.
+int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, float *ms) {
+    uint32_t k = (uint32_t)ss.size();
+    int rc = ensure_n_workspace(G);
+    if (rc) return rc;
+    rc = ensure_k_workspace(G, k);
+    if (rc) return rc;
+    Workspace &ws = G->ws;
+    cudaStream_t s = G->stream;
+    CK(cudaMemcpyAsync(ws.seeds, ss.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s));
+    SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far};
+    CK(cudaEventRecord(G->ev[0], s));
+    CK(launch_init(G->g, ws, k, s));
+    CK(cudaEventRecord(G->ev[1], s));
+    CK(launch_sssp(G->g, ws, G->geo, p, s));
+    CK(cudaEventRecord(G->ev[2], s));
+    CK(launch_scan(G->g, ws, k, full, s));
+    uint32_t launches = 4;      // init labels, init seeds, SSSP, scan
+    if (full) {
+        CK(launch_compact_pairs(ws, k, s));
+        CK(cudaEventRecord(G->ev[3], s));
+        CK(launch_mst(ws, k, G->geo, s));
+        CK(cudaEventRecord(G->ev[4], s));
+        CK(launch_tree(G->g, ws, k, ws.epoch_mark, G->nbits, s));
+        if (k > 1) launches += 3 + 1 + 2;   // compaction, MST, expansion + sort
+    } else {
+        CK(cudaEventRecord(G->ev[3], s));
+        CK(cudaEventRecord(G->ev[4], s));
+    }
+    CK(cudaEventRecord(G->ev[5], s));
+    CK(cudaMemcpyAsync(G->h_ctl, ws.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ms) {
+        for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], G->ev[i], G->ev[i + 1]);
+        ms[5] = (float)launches;
+    }
+    advance_epochs(ws, *G->h_ctl, s);
+    return STEINER_OK;
+}
+
+int fetch_tree(steiner_graph *G, steiner_result_t *out) {
+    const Control &c = *G->h_ctl;
+    uint32_t nt = std::min(c.n_tree, G->ws.tree_cap);
+    std::vector<uint64_t> keys(nt);
+    std::vector<uint32_t> ws(nt);
+    if (nt) {
+        CK(cudaMemcpyAsync(keys.data(), G->ws.tree_key, (size_t)nt * 8, cudaMemcpyDeviceToHost,
+                           G->stream));
+        CK(cudaMemcpyAsync(ws.data(), G->ws.tree_w, (size_t)nt * 4, cudaMemcpyDeviceToHost,
+                           G->stream));
+        CK(cudaStreamSynchronize(G->stream));
+    }
+    out->edges = nt ? (steiner_edge_t *)malloc((size_t)nt * sizeof(steiner_edge_t)) : nullptr;
+    if (nt && !out->edges) return fail(STEINER_ENOMEM, "host allocation of the result failed");
+    uint64_t mask = (1ull << G->nbits) - 1;
+    for (uint32_t i = 0; i < nt; ++i) {
+        out->edges[i].u = (uint32_t)(keys[i] >> G->nbits);
+        out->edges[i].v = (uint32_t)(keys[i] & mask);
+        out->edges[i].w = ws[i];
+    }
+    out->n_edges = nt;
+    out->total = c.total;
+    return STEINER_OK;
+}
+
+int query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_result_t *out,
+                 steiner_pair_t **pairs, uint64_t *n_pairs, steiner_stats_t *stats) {
+    out->edges = nullptr;
+    out->n_edges = 0;
+    out->total = 0;
+    std::vector<int32_t> ss;
+    int rc = sorted_seed_list(G, seeds, k, ss);
+    if (rc) return out->status = rc;
+    float ms[6] = {0, 0, 0, 0, 0, 0};
+    rc = run_pipeline(G, ss, true, ms);
+    if (rc) return out->status = rc;
+    const Control c = *G->h_ctl;
+    rc = status_from(c, k, true);
+    if (getenv("STEINER_TRACE")) {
+        fprintf(stderr, "[steiner] err=0x%x exit=%u iterations=%u phases=%u attempts=%llu\n",
+                c.err, c.exit_reason, c.iterations, c.phases, c.relax_attempts);
+        for (int i = 0; i < TRACE_LEN && i < (int)c.iterations + 1; ++i)
+            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u\n", i, c.trace[i][0],
+                    c.trace[i][1], c.trace[i][2], c.trace[i][3]);
+    }
+    if (rc == STEINER_OK || rc == STEINER_EDISCONNECTED) {
+        int rc2 = fetch_tree(G, out);
+        if (rc2) return out->status = rc2;
+    }
+    if (pairs && (rc == STEINER_OK || rc == STEINER_EDISCONNECTED)) {
+        uint32_t np = k > 1 ? c.n_pairs : 0;
+        std::vector<uint64_t> key(np);
+        std::vector<uint32_t> ra(np), rb(np), arc(np), mst(np);
+        if (np) {
+            cudaStream_t s = G->stream;
+            CK(cudaMemcpyAsync(key.data(), G->ws.e_key, (size_t)np * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(ra.data(), G->ws.e_ra, (size_t)np * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(rb.data(), G->ws.e_rb, (size_t)np * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(arc.data(), G->ws.e_arc, (size_t)np * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(mst.data(), G->ws.e_mst, (size_t)np * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        steiner_pair_t *p = (steiner_pair_t *)malloc(std::max<size_t>(np, 1) * sizeof(steiner_pair_t));
+        if (!p) return out->status = fail(STEINER_ENOMEM, "host allocation failed");
+        for (uint32_t i = 0; i < np; ++i) {
+            p[i].ra = ra[i];
+            p[i].rb = rb[i];
+            p[i].b = key[i] >> 32;
+            p[i].arc = arc[i];
+            p[i].in_mst = mst[i];
+        }
+        *pairs = p;
+        if (n_pairs) *n_pairs = np;
+    }
+    if (stats) {
+        stats->relax_attempts = c.relax_attempts;
+        stats->relax_improved = c.relax_improved;
+        stats->iterations = c.iterations;
+        stats->phases = c.phases;
+        stats->n_pairs = k > 1 ? c.n_pairs : 0;
+        stats->n_tree_edges = c.n_tree;
+        stats->gpu_launches = (uint32_t)ms[5];
+        stats->ms_init = ms[0];
+        stats->ms_voronoi = ms[1];
+        stats->ms_bridges = ms[2];
+        stats->ms_mst = ms[3];
+        stats->ms_tree = ms[4];
+    }
+    return out->status = rc;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported entry points
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *steiner_last_error(void) { return g_last_error.c_str(); }
+
+const char *steiner_version(void) { return "gb300-steiner 0.1 (sm_103a)"; }
+
+int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w, uint32_t n,
+                       uint64_t n_arcs, int device, steiner_graph_t *out) {
+    if (!out) return fail(STEINER_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!row_ptr || (n_arcs && (!col || !w))) return fail(STEINER_EINVAL, "null graph array");
+    if (n == 0) return fail(STEINER_EINVAL, "graph has no vertices");
+    if (n_arcs >= 0xFFFFFFFFull) return fail(STEINER_EINVAL, "arc count must be below 2^32");
+    if (row_ptr[0] != 0 || row_ptr[n] != n_arcs)
+        return fail(STEINER_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] the arc count");
+    for (uint32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return fail(STEINER_EINVAL, "row_ptr not monotone");
+    CK(cudaSetDevice(device));
+    steiner_graph *G = new steiner_graph();
+    G->device = device;
+    G->g.n = n;
+    G->g.m = n_arcs;
+    G->nbits = bits_for(n);
+    auto bail = [&](int rc) {
+        steiner_free_graph(G);
+        return rc;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    for (auto &ev : G->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaMallocHost((void **)&G->h_ctl, sizeof(Control))) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMallocHost"));
+    // heavy rows, listed in CHUNK-arc pieces
+    std::vector<uint64_t> chunks;
+    uint64_t cap = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        uint32_t deg = row_ptr[v + 1] - row_ptr[v];
+        if (deg >= HEAVY_DEG) {
+            uint32_t nc = (deg + CHUNK - 1) / CHUNK;
+            for (uint32_t c = 0; c < nc; ++c) chunks.push_back(((uint64_t)v << 32) | c);
+            cap += nc;
+        }
+    }
+    G->g.n_heavy_chunks = (uint32_t)chunks.size();
+    G->g.heavy_chunk_cap = (uint32_t)std::max<uint64_t>(cap, 1);
+    if ((e = dalloc(G->g.row_ptr, (uint64_t)n + 1)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if ((e = dalloc(G->g.adj, n_arcs)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if ((e = dalloc(G->g.heavy_chunks, chunks.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    int32_t *d_col = nullptr;
+    uint32_t *d_w = nullptr, *d_bad = nullptr;
+    if ((e = dalloc(d_col, n_arcs)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if ((e = dalloc(d_w, n_arcs)) != cudaSuccess) {
+        cudaFree(d_col);
+        return bail(cuda_fail(e, "cudaMalloc"));
+    }
+    if ((e = dalloc(d_bad, 1)) != cudaSuccess) {
+        cudaFree(d_col);
+        cudaFree(d_w);
+        return bail(cuda_fail(e, "cudaMalloc"));
+    }
+    cudaStream_t s = G->stream;
+    uint32_t bad = 0;
+    e = cudaMemcpyAsync(G->g.row_ptr, row_ptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_arcs)
+        e = cudaMemcpyAsync(d_col, col, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_arcs)
+        e = cudaMemcpyAsync(d_w, w, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !chunks.empty())
+        e = cudaMemcpyAsync(G->g.heavy_chunks, chunks.data(), chunks.size() * 8,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, s);
+    if (e == cudaSuccess) e = launch_validate_graph(G->g.row_ptr, d_col, d_w, n, n_arcs, G->g.adj, d_bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_col);
+    cudaFree(d_w);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "graph upload"));
+    if (bad) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "malformed graph (flags 0x%x: 1 range, 2 self-loop, 4 zero weight, "
+                 "8 unsorted/duplicate, 16 asymmetric)", bad);
+        return bail(fail(STEINER_EINVAL, msg));
+    }
+    // launch geometry of the persistent kernels
+    cudaDeviceGetAttribute(&G->geo.sm_count, cudaDevAttrMultiProcessorCount, device);
+    G->geo.threads = 256;
+    int per_sm = sssp_occupancy(256);
+    if (per_sm < 1) return bail(fail(STEINER_ECUDA, "SSSP kernel does not fit on an SM"));
+    G->geo.sssp_blocks = per_sm * G->geo.sm_count;
+    int mst_sm = mst_occupancy(512);
+    G->geo.mst_blocks = std::max(1, mst_sm) * G->geo.sm_count;
+    // default band width: ~32 average weights spread over the average degree
+    double avg_w = 0;
+    if (n_arcs) {
+        uint64_t step = std::max<uint64_t>(1, n_arcs / 65536), cnt = 0;
+        for (uint64_t i = 0; i < n_arcs; i += step, ++cnt) avg_w += w[i];
+        avg_w /= (double)cnt;
+    }
+    double avg_deg = n_arcs ? (double)n_arcs / n : 1.0;
+    double d = 32.0 * std::max(1.0, avg_w) / std::max(1.0, avg_deg);
+    G->delta = (uint32_t)std::min(std::max(d, 1.0), 1.0e9);
+    if (const char *env = getenv("STEINER_DELTA")) G->delta = (uint32_t)std::max(1L, atol(env));
+    *out = G;
+    return STEINER_OK;
+}
+
+void steiner_free_graph(steiner_graph_t G) {
+    if (!G) return;
+    if (G->serve) {
+        steiner_serve_stop(G);
+    }
+    destroy_batch(G->batch);
+    G->batch = nullptr;
+    cudaSetDevice(G->device);
+    if (G->stream) cudaStreamSynchronize(G->stream);
+    Workspace &ws = G->ws;
+    void *bufs[] = {ws.label, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.mark, ws.q[0], ws.q[1],
+                    ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
+                    ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
+                    ws.best, ws.tree_key, ws.tree_key2, ws.tree_w, ws.tree_w2, G->g.row_ptr,
+                    G->g.adj, G->g.heavy_chunks};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    for (auto &ev : G->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (G->h_ctl) cudaFreeHost(G->h_ctl);
+    if (G->stream) cudaStreamDestroy(G->stream);
+    delete G;
+}
+
+int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
+    if (!G || !key) return fail(STEINER_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(G->mu);
+    if (!strcmp(key, "delta")) {
+        if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "delta out of range");
+        G->delta = (uint32_t)value;
+    } else if (!strcmp(key, "max_iters")) {
+        if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "max_iters out of range");
+        G->max_iters = (uint32_t)value;
+    } else {
+        return fail(STEINER_EINVAL, std::string("unknown parameter ") + key);
+    }
+    return STEINER_OK;
+}
+
+int64_t steiner_get_param(steiner_graph_t G, const char *key) {
+    if (!G || !key) return -1;
+    if (!strcmp(key, "delta")) return G->delta;
+    if (!strcmp(key, "max_iters")) return G->max_iters;
+    if (!strcmp(key, "sssp_blocks")) return G->geo.sssp_blocks;
+    if (!strcmp(key, "sm_count")) return G->geo.sm_count;
+    if (!strcmp(key, "heavy_chunks")) return G->g.n_heavy_chunks;
+    return -1;
+}
+
+int steiner_query(steiner_graph_t G, const int32_t *seeds, uint32_t k, steiner_result_t *out) {
+    return steiner_query_detail(G, seeds, k, out, nullptr, nullptr, nullptr);
+}
+
+int steiner_query_detail(steiner_graph_t G, const int32_t *seeds, uint32_t k,
+                         steiner_result_t *out, steiner_pair_t **pairs, uint64_t *n_pairs,
+                         steiner_stats_t *stats) {
+    if (!G || !out) return fail(STEINER_EINVAL, "null argument");
+    if (pairs) *pairs = nullptr;
+    if (n_pairs) *n_pairs = 0;
+    std::lock_guard<std::mutex> lk(G->mu);
+    CK(cudaSetDevice(G->device));
+    return query_locked(G, seeds, k, out, pairs, n_pairs, stats);
+}
+
+int steiner_voronoi(steiner_graph_t G, const int32_t *seeds, uint32_t k, int32_t *cell,
+                    uint32_t *dist, int32_t *pred) {
+    if (!G) return fail(STEINER_EINVAL, "null graph");
+    std::lock_guard<std::mutex> lk(G->mu);
+    CK(cudaSetDevice(G->device));
+    std::vector<int32_t> ss;
+    int rc = sorted_seed_list(G, seeds, k, ss);
+    if (rc) return rc;
+    rc = run_pipeline(G, ss, false, nullptr);
+    if (rc) return rc;
+    Control c = *G->h_ctl;
+    rc = status_from(c, k, false);
+    if (rc) return rc;
+    uint32_t n = G->g.n;
+    cudaStream_t s = G->stream;
+    // device outputs are written in place; host outputs go through the
+    // (idle) tree buffers and are copied back
+    int32_t *d_cell = cell, *d_pred = pred;
+    uint32_t *d_dist = dist;
+    bool hc = cell && !is_device_ptr(cell), hd = dist && !is_device_ptr(dist),
+         hp = pred && !is_device_ptr(pred);
+    if (hc) d_cell = reinterpret_cast<int32_t *>(G->ws.tree_key);
+    if (hd) d_dist = reinterpret_cast<uint32_t *>(G->ws.tree_key2);
+    if (hp) d_pred = reinterpret_cast<int32_t *>(G->ws.tree_w);
+    CK(launch_export(G->g, G->ws, k, d_cell, d_dist, d_pred, s));
+    if (hc) CK(cudaMemcpyAsync(cell, d_cell, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    if (hd) CK(cudaMemcpyAsync(dist, d_dist, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    if (hp) CK(cudaMemcpyAsync(pred, d_pred, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return STEINER_OK;
+}
+
+void steiner_result_free(steiner_result_t *r) {
+    if (!r) return;
+    free(r->edges);
+    r->edges = nullptr;
+    r->n_edges = 0;
+}
+
+void steiner_pairs_free(steiner_pair_t *p) { free(p); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// helpers used by the batch and serving engines
+// ---------------------------------------------------------------------------
+
+namespace stn {
+
+int api_query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_result_t *out) {
+    return query_locked(G, seeds, k, out, nullptr, nullptr, nullptr);
+}
+
+std::mutex &api_mutex(steiner_graph *G) { return G->mu; }
+const DevGraph &api_graph(steiner_graph *G) { return G->g; }
+int api_device(steiner_graph *G) { return G->device; }
+BatchEngine *&api_batch(steiner_graph *G) { return G->batch; }
+ServeEngine *&api_serve(steiner_graph *G) { return G->serve; }
+uint32_t api_delta(steiner_graph *G) { return G->delta; }
+uint32_t api_nbits(steiner_graph *G) { return G->nbits; }
+const Geometry &api_geometry(steiner_graph *G) { return G->geo; }
+void api_set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace stn

@@ -1,0 +1,147 @@
+// Device-side helpers shared by the library's kernels: constants, the
+// bounded grid-wide barrier used by the persistent kernels, cache-global
+// loads for data other blocks write, and warp-level scans.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace stn {
+
+constexpr uint32_t INF32 = 0xFFFFFFFFu;
+constexpr uint64_t INF64 = ~0ull;
+constexpr uint32_t SEED_ARC = 0xFFFFFFFEu;   // pred_arc marker of a seed (pred = self)
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+// Device status bits, collected in Control::err and mapped to STEINER_E* on
+// the host.
+enum : uint32_t {
+    ERR_OVERFLOW = 1u,      // a distance or bridge sum reached 2^32 - 1
+    ERR_TIMEOUT = 2u,       // iteration cap hit
+    ERR_CAPACITY = 4u,      // an append would have overrun its buffer (skipped)
+    ERR_BARRIER = 8u,       // a grid barrier wait gave up
+};
+
+// Spin limit of a grid barrier wait (each spin sleeps ~64 ns): ~4 s.
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Loads that bypass L1: for values written by other blocks of a persistent
+// kernel (labels, queues, counters).
+__device__ __forceinline__ uint64_t ldcg_u64(const uint64_t *p) {
+    return __ldcg(reinterpret_cast<const unsigned long long *>(p));
+}
+__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
+
+// Grid-wide barrier for cooperatively launched kernels.  Every wait is
+// bounded: a block that waits longer than BARRIER_SPIN_LIMIT spins sets
+// ERR_BARRIER in *err and returns false; callers then leave their loop.
+// Once ERR_BARRIER is set every later barrier returns false too, so all
+// blocks leave within one more bounded wait.  Returns true on a normal
+// release.  Single-block grids use __syncthreads.
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, uint32_t *err) {
+    __shared__ int ok_s;
+    if (gridDim.x == 1) {
+        __syncthreads();
+        return true;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned int g = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar->count = 0;
+            __threadfence();
+            red_release_add_u32(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_u32(&bar->gen) == g) {
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    atomicOr(err, ERR_BARRIER);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        // a block that gave up earlier poisons every later barrier
+        if (ld_acquire_u32(err) & ERR_BARRIER) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan (all 32 lanes participate).
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane_id() >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+// Largest lane L whose value excl[L] <= j (excl non-decreasing across lanes).
+__device__ __forceinline__ uint32_t warp_owner_search(uint32_t excl, uint32_t j) {
+    uint32_t lo = 0;
+#pragma unroll
+    for (uint32_t step = 16; step >= 1; step >>= 1) {
+        uint32_t cand = lo + step;
+        uint32_t ev = __shfl_sync(FULL, excl, cand & 31u);
+        if (cand < 32 && ev <= j) lo = cand;
+    }
+    return lo;
+}
+
+// Warp-aggregated append: lanes with `want` get consecutive slots of a
+// queue whose fill counter is *count and capacity cap.  Returns the slot or
+// INF32 if the lane did not append or the queue was full (ERR_CAPACITY).
+__device__ __forceinline__ uint32_t warp_append(bool want, uint32_t *count, uint32_t cap,
+                                                uint32_t *err) {
+    uint32_t mask = __ballot_sync(FULL, want);
+    if (mask == 0) return INF32;
+    uint32_t leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+    base = __shfl_sync(FULL, base, leader);
+    if (!want) return INF32;
+    uint32_t slot = base + (uint32_t)__popc(mask & lanemask_lt());
+    if (slot >= cap) {
+        atomicOr(err, ERR_CAPACITY);
+        return INF32;
+    }
+    return slot;
+}
+
+// Slot of the seed pair (a, b), a < b < k, in the upper-triangle table:
+// ascending slot order is ascending (a, b) order.
+__host__ __device__ __forceinline__ uint64_t pair_slot(uint64_t a, uint64_t b, uint64_t k) {
+    return a * k - a * (a + 1) / 2 + (b - a - 1);
+}
+
+}  // namespace stn

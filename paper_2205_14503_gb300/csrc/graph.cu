@@ -1,0 +1,85 @@
+// Graph upload: device-side validation of the CSR (the paper's graphs are
+// symmetric with positive integer weights: Table "preliminaries_notation",
+// Section "Evaluation") and interleaving of (neighbour, weight) into one
+// 8-byte record per arc, so a relaxation reads one sector-aligned pair.
+#include "internal.h"
+
+namespace stn {
+
+enum : uint32_t {
+    BAD_RANGE = 1u,      // neighbour id out of range
+    BAD_SELF = 2u,       // self-loop
+    BAD_WEIGHT = 4u,     // weight 0
+    BAD_ORDER = 8u,      // row not strictly ascending (unsorted or duplicate)
+    BAD_SYMMETRY = 16u,  // reverse arc missing or with another weight
+};
+
+__device__ __forceinline__ bool find_reverse(const uint32_t *row_ptr, const int32_t *col,
+                                             const uint32_t *w, uint32_t v, uint32_t u,
+                                             uint32_t wt) {
+    uint32_t lo = row_ptr[v], hi = row_ptr[v + 1];
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        uint32_t c = (uint32_t)col[mid];
+        if (c == u) return w[mid] == wt;
+        if (c < u) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restrict__ row_ptr,
+                                                       const int32_t *__restrict__ col,
+                                                       const uint32_t *__restrict__ w,
+                                                       uint32_t n, uint2 *__restrict__ adj,
+                                                       uint32_t *bad) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t flags = 0;
+    for (uint32_t b0 = warp * 32; b0 < n; b0 += nwarps * 32) {
+        uint32_t u = b0 + lane;
+        uint32_t s = 0, deg = 0;
+        if (u < n) {
+            s = row_ptr[u];
+            deg = row_ptr[u + 1] - s;
+        }
+        uint32_t incl = warp_inclusive_scan(deg);
+        uint32_t excl = incl - deg;
+        uint32_t total = __shfl_sync(FULL, incl, 31);
+        for (uint32_t b = 0; b < total; b += 32) {
+            uint32_t j = b + lane;
+            bool valid = j < total;
+            uint32_t owner = warp_owner_search(excl, valid ? j : 0);
+            uint32_t so = __shfl_sync(FULL, s, owner);
+            uint32_t eo = __shfl_sync(FULL, excl, owner);
+            if (!valid) continue;
+            uint32_t src = b0 + owner;
+            uint32_t e = so + (j - eo);
+            int32_t c = col[e];
+            uint32_t wt = w[e];
+            adj[e] = make_uint2((uint32_t)c, wt);
+            if (c < 0 || (uint32_t)c >= n) {
+                flags |= BAD_RANGE;
+                continue;
+            }
+            if ((uint32_t)c == src) flags |= BAD_SELF;
+            if (wt == 0) flags |= BAD_WEIGHT;
+            if (e > so && col[e - 1] >= c) flags |= BAD_ORDER;
+            if (!find_reverse(row_ptr, col, w, (uint32_t)c, src, wt)) flags |= BAD_SYMMETRY;
+        }
+    }
+    if (flags) atomicOr(bad, flags);
+}
+
+cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                                  uint32_t n, uint64_t m, uint2 *adj, uint32_t *bad,
+                                  cudaStream_t s) {
+    (void)m;
+    uint64_t blocks = ((uint64_t)n + 255) / 256;
+    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    if (blocks < 1) blocks = 1;
+    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace stn

@@ -1,0 +1,128 @@
+// Internal interfaces between the C ABI (api.cu) and the kernel files.
+// Host-visible structs describe device buffers; launchers enqueue work on
+// a caller stream and never synchronise.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace stn {
+
+// Degree at or above which a vertex's adjacency is processed in chunks of
+// CHUNK arcs (one warp per chunk) instead of inside a 32-vertex batch.
+constexpr uint32_t HEAVY_DEG = 256;
+constexpr uint32_t CHUNK = 1024;
+
+// Resident graph: row offsets and interleaved (neighbour, weight) arcs.
+struct DevGraph {
+    uint32_t n = 0;
+    uint64_t m = 0;                 // arcs
+    uint32_t *row_ptr = nullptr;    // n + 1
+    uint2 *adj = nullptr;           // m: {col, w}
+    uint64_t *heavy_chunks = nullptr;   // (v << 32) | chunk index, for deg >= HEAVY_DEG
+    uint32_t n_heavy_chunks = 0;
+    uint32_t heavy_chunk_cap = 0;   // bound on chunk entries a frontier can hold
+};
+
+constexpr int TRACE_LEN = 64;
+
+// Device control block of one query.
+struct Control {
+    GridBarrier bar;
+    uint32_t err;
+    uint32_t near_count[3];
+    uint32_t heavy_count[3];
+    uint32_t far_count[2];
+    uint32_t far_min[2];
+    uint32_t iterations;
+    uint32_t phases;
+    unsigned long long relax_attempts;
+    unsigned long long relax_improved;
+    // bridge / tree phases
+    uint32_t n_pairs;
+    uint32_t n_mst;
+    uint32_t n_tree;
+    uint32_t pad;
+    unsigned long long total;
+    GridBarrier bar2;
+    uint32_t mst_any;
+    uint32_t exit_reason;        // 1 converged, 2 iteration cap, 3/4 barrier gave up
+    uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
+};
+
+// Per-query device workspace for the single-query path.
+struct Workspace {
+    uint32_t n = 0;
+    uint64_t *label = nullptr;      // (dist << 32) | rank
+    uint32_t *pred_arc = nullptr;   // arc of the pred edge in v's row; SEED_ARC; INF32
+    uint32_t *stamp_near = nullptr;
+    uint32_t *stamp_far = nullptr;
+    uint32_t *mark = nullptr;       // tree-walk stamps
+    uint32_t *q[2] = {nullptr, nullptr};      // light frontier
+    uint64_t *hq[2] = {nullptr, nullptr};     // heavy-chunk frontier
+    uint32_t *far[2] = {nullptr, nullptr};
+    Control *ctl = nullptr;
+    int32_t *seeds = nullptr;       // sorted seed ids (rank order)
+    uint32_t seeds_cap = 0;
+    uint64_t *pairtab = nullptr;    // k (k - 1) / 2 packed (b << 32 | arc)
+    uint64_t pairtab_cap = 0;
+    // compacted distance graph
+    uint64_t *e_key = nullptr;      // (b << 32) | slot
+    uint32_t *e_ra = nullptr, *e_rb = nullptr, *e_arc = nullptr;
+    uint32_t *e_mst = nullptr;
+    uint32_t *tile_off = nullptr;
+    uint64_t e_cap = 0;
+    uint32_t tile_cap = 0;
+    // MST scratch (k entries)
+    uint32_t *comp = nullptr, *hook = nullptr;
+    unsigned long long *best = nullptr;
+    uint32_t comp_cap = 0;
+    // tree output
+    uint64_t *tree_key = nullptr, *tree_key2 = nullptr;   // (min << 32) | max
+    uint32_t *tree_w = nullptr, *tree_w2 = nullptr;
+    uint32_t tree_cap = 0;
+    // tags that avoid clearing the stamp arrays between queries
+    uint32_t epoch_near = 0, epoch_far = 0, epoch_mark = 0;
+};
+
+// Launch geometry of the persistent kernels (from the occupancy API).
+struct Geometry {
+    int sm_count = 0;
+    int sssp_blocks = 0;
+    int mst_blocks = 0;
+    int threads = 256;
+};
+
+struct SsspParams {
+    uint32_t delta;          // near/far band width
+    uint32_t max_iters;      // loop cap -> ERR_TIMEOUT
+    uint32_t base_near;      // first near tag of this query
+    uint32_t base_far;       // first far tag of this query
+};
+
+// voronoi.cu
+cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, cudaStream_t s);
+cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
+                        const SsspParams &p, cudaStream_t s);
+cudaError_t launch_export(const DevGraph &g, Workspace &ws, uint32_t k, int32_t *cell,
+                          uint32_t *dist, int32_t *pred, cudaStream_t s);
+int sssp_occupancy(int threads);
+
+// bridge.cu
+cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs,
+                        cudaStream_t s);
+cudaError_t launch_compact_pairs(Workspace &ws, uint32_t k, cudaStream_t s);
+
+// tree.cu
+cudaError_t launch_mst(Workspace &ws, uint32_t k, const Geometry &geo, cudaStream_t s);
+cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t tag,
+                        uint32_t n_bits, cudaStream_t s);
+int mst_occupancy(int threads);
+
+// graph.cu
+cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col,
+                                  const uint32_t *w, uint32_t n, uint64_t m, uint2 *adj,
+                                  uint32_t *bad, cudaStream_t s);
+
+}  // namespace stn

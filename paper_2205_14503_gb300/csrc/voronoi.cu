@@ -1,0 +1,438 @@
+// Voronoi cells of all seeds at once (Algorithm 2 Step 1; Algorithm 4 is the
+// paper's asynchronous vertex-centric form of the same fixed point).
+//
+// Every vertex v holds one packed label (d1(src(v), v) << 32) | rank(src(v)).
+// Relaxing an arc u -> v proposes (d(u) + d(u,v)) << 32 | rank(u) and keeps
+// the minimum with a 64-bit atomicMin, so the fixed point is, per vertex,
+// the lexicographic minimum over seeds of (distance, seed rank): the
+// nearest seed, ties to the smallest seed id.  The fixed point does not
+// depend on the order in which relaxations land.
+//
+// Order of work: a near/far frontier (a two-bucket delta-stepping).  The
+// paper prioritises low-distance messages in its message queue (Section
+// "Distributed Implementation"); on the GPU the same effect comes from
+// relaxing only vertices whose distance is below a threshold T (near) and
+// parking the rest (far) until the near frontier drains, then raising T by
+// delta.  One persistent cooperative kernel runs all iterations with a
+// bounded grid barrier between them.
+#include "internal.h"
+
+namespace stn {
+
+struct SsspArgs {
+    const uint32_t *__restrict__ row_ptr;
+    const uint2 *__restrict__ adj;
+    uint32_t n;
+    uint64_t *label;
+    uint32_t *stamp_near;
+    uint32_t *stamp_far;
+    uint32_t *q0, *q1;
+    uint64_t *hq0, *hq1;
+    uint32_t *far0, *far1;
+    Control *ctl;
+    uint32_t delta;
+    uint32_t max_iters;
+    uint32_t base_near;
+    uint32_t base_far;
+    uint32_t heavy_cap;
+};
+
+// ---------------------------------------------------------------------------
+// init (Algorithm 3, INITIALIZATION): every label at infinity, then each
+// seed at distance 0 in its own cell and on the first frontier.
+// ---------------------------------------------------------------------------
+
+__global__ void init_labels_kernel(uint32_t n, uint64_t *__restrict__ label,
+                                   uint32_t *__restrict__ pred_arc) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        label[v] = INF64;
+        pred_arc[v] = INF32;
+    }
+}
+
+__global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const int32_t *seeds,
+                                  uint32_t k, uint64_t *label, uint32_t *pred_arc,
+                                  uint32_t *stamp_near, uint32_t tag0, uint32_t *q0,
+                                  uint64_t *hq0, uint32_t heavy_cap, uint32_t n, Control *ctl) {
+    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) {
+        ctl->far_min[0] = INF32;
+        ctl->far_min[1] = INF32;
+    }
+    if (r >= k) return;
+    uint32_t s = (uint32_t)seeds[r];
+    label[s] = (uint64_t)r;               // distance 0, cell = rank r
+    pred_arc[s] = SEED_ARC;
+    stamp_near[s] = tag0;
+    uint32_t rs = row_ptr[s], deg = row_ptr[s + 1] - rs;
+    if (deg >= HEAVY_DEG) {
+        uint32_t nc = (deg + CHUNK - 1) / CHUNK;
+        uint32_t base = atomicAdd(&ctl->heavy_count[0], nc);
+        if (base + nc > heavy_cap) { atomicOr(&ctl->err, ERR_CAPACITY); return; }
+        for (uint32_t c = 0; c < nc; ++c) hq0[base + c] = ((uint64_t)s << 32) | c;
+    } else {
+        uint32_t slot = atomicAdd(&ctl->near_count[0], 1u);
+        if (slot >= n) { atomicOr(&ctl->err, ERR_CAPACITY); return; }
+        q0[slot] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// relaxation of one arc per lane, with warp-aggregated frontier appends
+// ---------------------------------------------------------------------------
+
+struct PushTargets {
+    uint32_t *qn;        // light queue of the next iteration
+    uint32_t *qn_count;
+    uint64_t *hqn;       // heavy-chunk queue of the next iteration
+    uint32_t *hqn_count;
+    uint32_t *farq;      // far pile of the current phase
+    uint32_t *far_count;
+    uint32_t *far_min;
+    uint32_t tag_next;
+    uint32_t tag_far;
+    uint64_t T;
+};
+
+// Appends v (a lane's candidate) to the light or heavy near queue.  All
+// lanes of the warp must call it.
+__device__ __forceinline__ void push_near(const SsspArgs &a, const PushTargets &t, bool want,
+                                          uint32_t v) {
+    bool heavy = false;
+    uint32_t nc = 0;
+    if (want) {
+        uint32_t deg = a.row_ptr[v + 1] - a.row_ptr[v];
+        if (deg >= HEAVY_DEG) {
+            heavy = true;
+            nc = (deg + CHUNK - 1) / CHUNK;
+        }
+    }
+    uint32_t slot = warp_append(want && !heavy, t.qn_count, a.n, &a.ctl->err);
+    if (slot != INF32) t.qn[slot] = v;
+    if (heavy) {
+        uint32_t base = atomicAdd(t.hqn_count, nc);
+        if (base + nc > a.heavy_cap) {
+            atomicOr(&a.ctl->err, ERR_CAPACITY);
+        } else {
+            for (uint32_t c = 0; c < nc; ++c) t.hqn[base + c] = ((uint64_t)v << 32) | c;
+        }
+    }
+}
+
+__device__ __forceinline__ void relax_arc(const SsspArgs &a, const PushTargets &t, bool valid,
+                                          uint32_t arc, uint64_t du, uint32_t cu,
+                                          unsigned long long &attempts,
+                                          unsigned long long &improved) {
+    bool to_near = false, to_far = false;
+    uint32_t v = 0, nd32 = INF32;
+    if (valid) {
+        uint2 e = __ldg(&a.adj[arc]);
+        v = e.x;
+        uint64_t nd = du + (uint64_t)e.y;
+        ++attempts;
+        if (nd < INF32) {          // a longer proposal is skipped; see the overflow check in the scan
+            uint64_t nl = (nd << 32) | cu;
+            if (nl < ldcg_u64(&a.label[v])) {
+                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[v]),
+                                         (unsigned long long)nl);
+                if (nl < old) {
+                    ++improved;
+                    if (nd < t.T) {
+                        to_near = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
+                    } else {
+                        to_far = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
+                        nd32 = (uint32_t)nd;
+                    }
+                }
+            }
+        }
+    }
+    push_near(a, t, to_near, v);
+    uint32_t slot = warp_append(to_far, t.far_count, a.n, &a.ctl->err);
+    if (slot != INF32) t.farq[slot] = v;
+    if (__any_sync(FULL, to_far)) {
+        uint32_t m = nd32;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
+        if (lane_id() == 0 && m != INF32) atomicMin(t.far_min, m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent near/far kernel
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    Control *ctl = a.ctl;
+    unsigned long long attempts = 0, improved = 0;
+    uint32_t it = 0, phase = 0;
+    uint64_t T = a.delta;
+    bool first = (blockIdx.x == 0 && threadIdx.x == 0);
+
+    for (;;) {
+        const uint32_t cs = it % 3, ns = (it + 1) % 3;
+        uint32_t n_light = min(ldcg_u32(&ctl->near_count[cs]), a.n);
+        uint32_t n_heavy = min(ldcg_u32(&ctl->heavy_count[cs]), a.heavy_cap);
+        if (first) {
+            ctl->near_count[(it + 2) % 3] = 0;
+            ctl->heavy_count[(it + 2) % 3] = 0;
+        }
+        const bool odd = it & 1;
+        const uint32_t *qc = odd ? a.q1 : a.q0;
+        const uint64_t *hqc = odd ? a.hq1 : a.hq0;
+        const uint32_t fc = phase & 1;
+        PushTargets t;
+        t.qn = odd ? a.q0 : a.q1;
+        t.qn_count = &ctl->near_count[ns];
+        t.hqn = odd ? a.hq0 : a.hq1;
+        t.hqn_count = &ctl->heavy_count[ns];
+        t.farq = fc ? a.far1 : a.far0;
+        t.far_count = &ctl->far_count[fc];
+        t.far_min = &ctl->far_min[fc];
+        t.tag_next = a.base_near + it + 1;
+        t.tag_far = a.base_far + phase;
+        t.T = T;
+
+        if (first && it < TRACE_LEN) {
+            ctl->trace[it][0] = n_light;
+            ctl->trace[it][1] = n_heavy;
+            ctl->trace[it][2] = ldcg_u32(&ctl->far_count[phase & 1]);
+            ctl->trace[it][3] = (uint32_t)T;
+        }
+        const uint32_t n_work = n_heavy + (n_light + 31) / 32;
+        for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
+            if (wi < n_heavy) {
+                // one CHUNK of a high-degree vertex per warp
+                uint64_t item = __ldcg(reinterpret_cast<const unsigned long long *>(&hqc[wi]));
+                uint32_t u = (uint32_t)(item >> 32), c = (uint32_t)item;
+                uint32_t s = a.row_ptr[u] + c * CHUNK;
+                uint32_t e = min(a.row_ptr[u + 1], s + CHUNK);
+                uint64_t lab = ldcg_u64(&a.label[u]);
+                for (uint32_t b = s; b < e; b += 32) {
+                    uint32_t arc = b + lane;
+                    relax_arc(a, t, arc < e, arc, lab >> 32, (uint32_t)lab, attempts, improved);
+                }
+            } else {
+                // 32 frontier vertices per warp, their arcs flattened over the lanes
+                uint32_t i = (wi - n_heavy) * 32 + lane;
+                bool has = i < n_light;
+                uint32_t s = 0, deg = 0;
+                uint64_t lab = INF64;
+                if (has) {
+                    uint32_t u = ldcg_u32(&qc[i]);
+                    s = a.row_ptr[u];
+                    deg = a.row_ptr[u + 1] - s;
+                    lab = ldcg_u64(&a.label[u]);
+                    if (lab == INF64) deg = 0;
+                }
+                uint32_t incl = warp_inclusive_scan(deg);
+                uint32_t excl = incl - deg;
+                uint32_t total = __shfl_sync(FULL, incl, 31);
+                for (uint32_t b = 0; b < total; b += 32) {
+                    uint32_t j = b + lane;
+                    bool valid = j < total;
+                    uint32_t owner = warp_owner_search(excl, valid ? j : 0);
+                    uint32_t so = __shfl_sync(FULL, s, owner);
+                    uint32_t eo = __shfl_sync(FULL, excl, owner);
+                    uint64_t lo = __shfl_sync(FULL, lab, owner);
+                    relax_arc(a, t, valid, so + (j - eo), lo >> 32, (uint32_t)lo, attempts,
+                              improved);
+                }
+            }
+        }
+        if (!grid_sync(&ctl->bar, &ctl->err)) {
+            if (first) ctl->exit_reason = 3;
+            break;
+        }
+        ++it;
+        if (it >= a.max_iters) {
+            if (first) {
+                atomicOr(&ctl->err, ERR_TIMEOUT);
+                ctl->exit_reason = 2;
+            }
+            break;
+        }
+        uint32_t next = ldcg_u32(&ctl->near_count[ns]) + ldcg_u32(&ctl->heavy_count[ns]);
+        if (next != 0) continue;
+
+        // Near frontier drained: raise the threshold and split the far pile.
+        // Every block has just read near_count[it % 3] to take this branch,
+        // so the split must not push there: it fills the slot (and queue)
+        // of iteration it + 1, and the loop resumes at it + 1.  That slot was
+        // cleared at the top of iteration it - 1 and nothing reads it before
+        // the barrier that ends the split.  Iteration it + 1 will push into
+        // slot (it + 2) % 3, which the skipped top of iteration it would
+        // have cleared: clear it here (its last reader was iteration it - 1).
+        uint32_t nf = min(ldcg_u32(&ctl->far_count[fc]), a.n);
+        if (nf == 0) {                                        // converged
+            if (first) ctl->exit_reason = 1;
+            break;
+        }
+        uint32_t fmin = ldcg_u32(&ctl->far_min[fc]);
+        uint64_t T_old = T;
+        T = (fmin != INF32 && (uint64_t)fmin > T ? (uint64_t)fmin : T) + a.delta;
+        ++phase;
+        const uint32_t *fs = fc ? a.far1 : a.far0;
+        const uint32_t its = it + 1;
+        if (first) {
+            ctl->near_count[(its + 1) % 3] = 0;
+            ctl->heavy_count[(its + 1) % 3] = 0;
+        }
+        PushTargets u;
+        u.qn = (its & 1) ? a.q1 : a.q0;
+        u.qn_count = &ctl->near_count[its % 3];
+        u.hqn = (its & 1) ? a.hq1 : a.hq0;
+        u.hqn_count = &ctl->heavy_count[its % 3];
+        u.farq = fc ? a.far0 : a.far1;
+        u.far_count = &ctl->far_count[fc ^ 1];
+        u.far_min = &ctl->far_min[fc ^ 1];
+        u.tag_next = a.base_near + its;
+        u.tag_far = a.base_far + phase;
+        u.T = T;
+        for (uint32_t b = warp * 32; b < nf; b += nwarps * 32) {
+            uint32_t i = b + lane;
+            bool valid = i < nf;
+            uint32_t v = 0;
+            uint64_t d = INF32;
+            if (valid) {
+                v = ldcg_u32(&fs[i]);
+                d = ldcg_u64(&a.label[v]) >> 32;
+            }
+            bool to_near = valid && d >= T_old && d < T;     // below T_old: already settled
+            bool keep = valid && d >= T;
+            if (to_near) to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
+            if (keep) keep = atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
+            push_near(a, u, to_near, v);
+            uint32_t slot = warp_append(keep, u.far_count, a.n, &ctl->err);
+            if (slot != INF32) u.farq[slot] = v;
+            uint32_t m = keep ? (uint32_t)d : INF32;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
+            if (lane == 0 && m != INF32) atomicMin(u.far_min, m);
+        }
+        if (!grid_sync(&ctl->bar, &ctl->err)) {
+            if (first) ctl->exit_reason = 4;
+            break;
+        }
+        if (first) {
+            ctl->far_count[fc] = 0;
+            ctl->far_min[fc] = INF32;
+        }
+        it = its;
+        if (it >= a.max_iters) {
+            if (first) {
+                atomicOr(&ctl->err, ERR_TIMEOUT);
+                ctl->exit_reason = 2;
+            }
+            break;
+        }
+    }
+    // counters
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        attempts += __shfl_xor_sync(FULL, attempts, o);
+        improved += __shfl_xor_sync(FULL, improved, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&ctl->relax_attempts, attempts);
+        atomicAdd(&ctl->relax_improved, improved);
+    }
+    if (first) {
+        ctl->iterations = it;
+        ctl->phases = phase;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// export: packed labels -> (cell seed id, distance, predecessor id)
+// ---------------------------------------------------------------------------
+
+__global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
+                              const uint64_t *__restrict__ label,
+                              const uint32_t *__restrict__ pred_arc,
+                              const int32_t *__restrict__ seeds, int32_t *cell, uint32_t *dist,
+                              int32_t *pred) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint64_t lab = label[v];
+        if (lab == INF64) {
+            if (cell) cell[v] = -1;
+            if (dist) dist[v] = INF32;
+            if (pred) pred[v] = -1;
+            continue;
+        }
+        if (cell) cell[v] = seeds[(uint32_t)lab];
+        if (dist) dist[v] = (uint32_t)(lab >> 32);
+        if (pred) {
+            uint32_t pa = pred_arc[v];
+            pred[v] = pa == SEED_ARC ? (int32_t)v : (pa == INF32 ? -1 : (int32_t)adj[pa].x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static int grid_for(uint64_t items, int threads) {
+    uint64_t b = (items + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152ull * 16) b = 152ull * 16;
+    return (int)b;
+}
+
+cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ws.ctl, 0, sizeof(Control), s);
+    if (e != cudaSuccess) return e;
+    init_labels_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, ws.label, ws.pred_arc);
+    init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, ws.seeds, k, ws.label,
+                                                       ws.pred_arc, ws.stamp_near,
+                                                       ws.epoch_near, ws.q[0], ws.hq[0],
+                                                       g.heavy_chunk_cap, g.n, ws.ctl);
+    return cudaGetLastError();
+}
+
+int sssp_occupancy(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, threads, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
+                        const SsspParams &p, cudaStream_t s) {
+    SsspArgs a;
+    a.row_ptr = g.row_ptr;
+    a.adj = g.adj;
+    a.n = g.n;
+    a.label = ws.label;
+    a.stamp_near = ws.stamp_near;
+    a.stamp_far = ws.stamp_far;
+    a.q0 = ws.q[0];
+    a.q1 = ws.q[1];
+    a.hq0 = ws.hq[0];
+    a.hq1 = ws.hq[1];
+    a.far0 = ws.far[0];
+    a.far1 = ws.far[1];
+    a.ctl = ws.ctl;
+    a.delta = p.delta;
+    a.max_iters = p.max_iters;
+    a.base_near = p.base_near;
+    a.base_far = p.base_far;
+    a.heavy_cap = g.heavy_chunk_cap;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(geo.sssp_blocks),
+                                       dim3(geo.threads), args, 0, s);
+}
+
+cudaError_t launch_export(const DevGraph &g, Workspace &ws, uint32_t k, int32_t *cell,
+                          uint32_t *dist, int32_t *pred, cudaStream_t s) {
+    (void)k;
+    export_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.adj, ws.label, ws.pred_arc,
+                                                      ws.seeds, cell, dist, pred);
+    return cudaGetLastError();
+}
+
+}  // namespace stn

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element and bit-exact (all results are integers): per-vertex
+cell / distance / predecessor, the distance graph G'_1 (pairs, bridge
+distance, arc), the MST pairs, the tree edge list and its total distance,
+and the status codes of the degenerate cases."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2205_14503_gb300.workloads as wl
+from tests import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+st = pytest.importorskip("paper_2205_14503_gb300.steiner")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_14503_gb300 import build
+    build.build()
+    st.load_library()
+
+
+def _compare(g, seeds, detail=True):
+    """Run both sides; assert bit-exact agreement; return the oracle result."""
+    ref = oracle.steiner(g, seeds, want_labels=True, want_pairs=detail)
+    with st.SteinerGraph(g) as Gd:
+        rc, cell, dist, pred = Gd.voronoi(seeds)
+        res = Gd.query_detail(seeds) if detail else Gd.query(seeds)
+    assert res.status == ref.status, (res.status, ref.status, st.last_error())
+    if ref.status in (oracle.OK, oracle.EDISCONNECTED):
+        assert rc == st.STEINER_OK
+        np.testing.assert_array_equal(cell, ref.cell)
+        np.testing.assert_array_equal(dist, ref.dist)
+        np.testing.assert_array_equal(pred, ref.pred)
+        np.testing.assert_array_equal(res.edges, ref.edges)
+        assert res.total == ref.total
+        if detail:
+            np.testing.assert_array_equal(res.pairs[:, :4], ref.pairs)
+            mst_gpu = {(int(a), int(b)) for a, b, _, _, m in res.pairs.tolist() if m}
+            mst_ref = {(int(a), int(b)) for a, b, _, _ in ref.mst.tolist()}
+            assert mst_gpu == mst_ref
+    return ref
+
+
+def _cases():
+    yield "rmat9", wl.rmat(9, 8, wmax=100, seed=11), [1, 2, 12, 60]
+    yield "rmat10_unit", wl.rmat(10, 8, wmax=1, seed=12), [3, 9, 100]
+    yield "rmat11_w3", wl.rmat(11, 16, wmax=3, seed=13), [5, 30, 400]
+    yield "grid23x17", wl.grid(23, 17, 1000, seed=14), [2, 7, 40]
+    yield "grid_unit", wl.grid(40, 31, 1, seed=15), [2, 5, 64]
+    yield "connected", G.random_connected(3000, 2000, 1, 50, 16), [20, 200]
+    yield "complete", G.complete(60, 1, 10, 17), [6, 60]
+    yield "disconnected", G.random_graph(4000, 3000, 1, 20, 18), [25, 300]
+    yield "star", G.star(3000, 1, 5, 19), [10, 500]
+    yield "path", G.path(2000, 1, 9, 20), [2, 4, 33]
+    yield "tree", G.random_tree(5000, 1, 100, 21), [3, 50]
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,g,ks", CASES, ids=[c[0] for c in CASES])
+def test_parity_small_graphs(name, g, ks):
+    for i, k in enumerate(ks):
+        seeds = G.seeds_from(np.arange(g.n), k, 1000 + 17 * i + k)
+        _compare(g, seeds)
+
+
+def test_parity_rmat_scale16_k16():
+    """R-MAT scale 16, edge factor 16, weights [1,100], 16 seeds from the
+    largest component (the plain single-query workload)."""
+    g = wl.config_graph(1)
+    (seeds,) = wl.config_seed_sets(1, g)
+    ref = _compare(g, seeds)
+    assert ref.status == oracle.OK
+
+
+def test_parity_hubs_and_many_seeds():
+    """Heavy rows (degree >= 256, chunked), a multi-block MST (k > 362) and
+    a large pair table."""
+    g = wl.rmat(16, 16, wmax=1000, seed=99)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 2000, 3)
+    _compare(g, seeds)
+
+
+def test_parity_unit_weights_maximal_ties():
+    g = wl.rmat(15, 16, wmax=1, seed=5)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 300, 4)
+    _compare(g, seeds)
+
+
+def test_single_seed_and_all_vertices_seeded():
+    g = wl.grid(30, 20, 50, seed=3)
+    ref = _compare(g, [123])
+    assert ref.edges.shape[0] == 0 and ref.total == 0
+    _compare(g, np.arange(g.n))
+
+
+def test_seed_order_does_not_matter():
+    g = wl.rmat(12, 16, wmax=100, seed=8)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 40, 8)
+    with st.SteinerGraph(g) as Gd:
+        a = Gd.query(seeds)
+        b = Gd.query(seeds[::-1])
+        c = Gd.query(np.roll(seeds, 7))
+    assert np.array_equal(a.edges, b.edges) and np.array_equal(a.edges, c.edges)
+    assert a.total == b.total == c.total
+
+
+def test_repeated_queries_reuse_workspace():
+    """Back-to-back queries of different sizes on one handle (stamp epochs,
+    pair-table regrowth) give the oracle's answer every time."""
+    g = wl.rmat(13, 16, wmax=200, seed=9)
+    pool = wl.largest_cc(g)
+    with st.SteinerGraph(g) as Gd:
+        for i, k in enumerate([5, 300, 2, 50, 300, 1, 17]):
+            seeds = wl.sample_distinct(pool, k, 100 + i)
+            res = Gd.query(seeds)
+            ref = oracle.steiner(g, seeds, want_labels=False)
+            assert res.status == ref.status
+            np.testing.assert_array_equal(res.edges, ref.edges)
+            assert res.total == ref.total
+
+
+def test_invalid_seed_lists_are_rejected():
+    g = wl.grid(8, 8, 9, seed=1)
+    with st.SteinerGraph(g) as Gd:
+        assert Gd.query([]).status == st.STEINER_EINVAL
+        assert Gd.query([3, 3]).status == st.STEINER_EINVAL
+        assert Gd.query([64]).status == st.STEINER_EINVAL
+        assert Gd.query([-1, 5]).status == st.STEINER_EINVAL
+        assert Gd.query([0, 63]).status == st.STEINER_OK
+
+
+def test_overflow_and_disconnected_statuses():
+    big = 0xFFFFFFFF // 2 + 1
+    g = wl.from_edges(4, [0, 1, 2], [1, 2, 3], [big, big, 5])
+    _compare(g, [0, 3], detail=False)
+    g = wl.from_edges(3, [0, 1], [1, 2], [0xFFFFFFFE, 1])
+    _compare(g, [0, 2], detail=False)
+    g = wl.from_edges(2, [0], [1], [0xFFFFFFFE])
+    _compare(g, [0, 1])
+    e = np.array([[0, 1, 3], [1, 2, 4], [3, 4, 5], [4, 5, 1]])
+    g = wl.from_edges(7, e[:, 0], e[:, 1], e[:, 2])
+    ref = _compare(g, [0, 2, 3, 5])
+    assert ref.status == oracle.EDISCONNECTED
+
+
+def test_malformed_graphs_are_rejected_at_load():
+    g = wl.grid(6, 5, 9, seed=2)
+
+    def bad(mod):
+        rp, col, w = g.row_ptr.copy(), g.col.copy(), g.w.copy()
+        mod(rp, col, w)
+        with pytest.raises(st.SteinerError) as ei:
+            st.steiner_load_graph(rp, col, w)
+        assert ei.value.code == st.STEINER_EINVAL
+
+    bad(lambda rp, col, w: w.__setitem__(3, 0))
+    bad(lambda rp, col, w: w.__setitem__(3, w[3] + 1))
+    bad(lambda rp, col, w: col.__setitem__(0, 0))
+    bad(lambda rp, col, w: (col.__setitem__(0, col[1]), col.__setitem__(1, col[0])))
+    bad(lambda rp, col, w: col.__setitem__(2, 10 ** 6))
+    h = st.steiner_load_graph(g.row_ptr, g.col, g.w)
+    st.steiner_free_graph(h)
+
+
+def test_voronoi_into_device_tensors():
+    import torch
+    g = wl.rmat(12, 16, wmax=50, seed=4)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 9, 4)
+    ref = oracle.voronoi(g, seeds)
+    cell = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with st.SteinerGraph(g) as Gd:
+        rc, _, _, _ = Gd.voronoi(seeds, cell, dist, pred)
+    assert rc == st.STEINER_OK
+    np.testing.assert_array_equal(cell.cpu().numpy(), ref.cell)
+    np.testing.assert_array_equal(dist.cpu().numpy().view(np.uint32), ref.dist)
+    np.testing.assert_array_equal(pred.cpu().numpy(), ref.pred)
+
+
+@pytest.mark.parametrize("delta", [1, 7, 100, 5000, 10 ** 8])
+def test_result_is_independent_of_delta(delta):
+    """The near/far band width changes the schedule, never the fixed point."""
+    g = wl.rmat(13, 16, wmax=1000, seed=6)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 64, 6)
+    ref = oracle.steiner(g, seeds)
+    with st.SteinerGraph(g) as Gd:
+        Gd.set_param("delta", delta)
+        rc, cell, dist, pred = Gd.voronoi(seeds)
+        res = Gd.query(seeds)
+    np.testing.assert_array_equal(cell, ref.cell)
+    np.testing.assert_array_equal(pred, ref.pred)
+    np.testing.assert_array_equal(res.edges, ref.edges)
+
+
+def test_iteration_cap_reports_timeout():
+    """A loop cap that cannot be met returns STEINER_ETIMEOUT (bounded
+    device loops; no hang) and the handle stays usable."""
+    g = G.path(5000, 1, 9, 3)
+    with st.SteinerGraph(g) as Gd:
+        Gd.set_param("max_iters", 10)
+        assert Gd.query([0, 4999]).status == st.STEINER_ETIMEOUT
+        Gd.set_param("max_iters", 1 << 22)
+        res = Gd.query([0, 4999])
+    ref = oracle.steiner(g, [0, 4999], want_labels=False)
+    assert res.status == st.STEINER_OK and res.total == ref.total
