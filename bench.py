@@ -152,10 +152,17 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def workload(rank: int):
+def workload(rank: int, side: int | None = None, k: int | None = None):
+    """The benchmark graph and seed set.  ``side``/``k`` shrink the grid for
+    profiling captures (same seed density); the default is the workload."""
     import paper_2205_14503_gb300.workloads as wl
-    g = wl.config_graph(WORKLOAD)
-    (seeds,) = wl.config_seed_sets(WORKLOAD, g)
+    if side:
+        g = wl.grid(side, side, 1000, wl.CONFIG_SEED + WORKLOAD)
+        seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), k or 64,
+                                   (wl.CONFIG_SEED + WORKLOAD) ^ 0x51ED)
+    else:
+        g = wl.config_graph(WORKLOAD)
+        (seeds,) = wl.config_seed_sets(WORKLOAD, g)
     if rank > 0:    # replicas run their own queries of the same size
         seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), seeds.size,
                                    0x5EED + WORKLOAD + 1000 * rank)
@@ -177,9 +184,12 @@ def cpu_oracle_time(g, seeds, budget_s: float = 30.0):
 
 
 def config_dict(g, seeds):
-    return {"workload": "grid4096_k256", "graph": "4096x4096 4-connected grid, w~U[1,1000]",
+    side = int(round(g.n ** 0.5))
+    return {"workload": f"grid{side}_k{seeds.size}",
+            "graph": f"{side}x{side} 4-connected grid, w~U[1,1000]",
             "n": int(g.n), "arcs": int(g.n_arcs), "k": int(seeds.size),
-            "l2": "inputs larger than L2 (adjacency 537 MB, labels 134 MB)"}
+            "l2": f"inputs larger than L2 (adjacency {g.n_arcs * 8 >> 20} MiB, "
+                  f"labels {g.n * 8 >> 20} MiB)"}
 
 
 METRIC = "Steiner trees/s (Voronoi SSSP + bridge scan + MST + expansion)"
@@ -188,7 +198,7 @@ METRIC = "Steiner trees/s (Voronoi SSSP + bridge scan + MST + expansion)"
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    g, seeds = workload(0)
+    g, seeds = workload(0, args.side, args.k)
     import oracle
     for _ in range(args.warmup):
         oracle.steiner(g, seeds, want_labels=False)
@@ -220,7 +230,7 @@ def run_ours(args, world, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)
-    g, seeds = workload(rank)
+    g, seeds = workload(rank, args.side, args.k)
     t0 = time.perf_counter()
     G = st.SteinerGraph(g, device=local)
     load_s = time.perf_counter() - t0
@@ -317,6 +327,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=None,
+                    help="profiling only: a side x side grid instead of the workload")
+    ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     try:
