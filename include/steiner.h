@@ -192,6 +192,37 @@ int steiner_serve_stop(steiner_graph_t g);
 int steiner_set_param(steiner_graph_t g, const char *key, int64_t value);
 int64_t steiner_get_param(steiner_graph_t g, const char *key);
 
+/*
+ * steiner_voronoi_noalloc — the Voronoi cells of steiner_voronoi for callers
+ * that cannot allocate device memory (a framework that owns every device
+ * allocation through its own pool, or code that must not grow its device
+ * footprint after start-up).  This call allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  Its working memory is one
+ * fixed array of device memory inside the library (24 MiB + 256 bytes),
+ * present on every GPU that loads the library until the process exits.
+ * The paper has no counterpart to this entry point.
+ *   row_ptr, col, w  device, the CSR of the graph in the steiner_load_graph
+ *                    format (not re-validated; neighbour ids are range-checked)
+ *   n, n_arcs        sizes; n <= STEINER_NOALLOC_MAX_VERTICES
+ *   seeds            device, k distinct seed ids in ASCENDING order
+ *   cell, dist, pred device outputs, n entries each (may be NULL), same
+ *                    meaning as in steiner_voronoi
+ *   stream           a cudaStream_t (NULL = the legacy default stream); the
+ *                    call returns after the stream has finished the work
+ * The first call on a device looks up the array's device address and the
+ * launch size (cudaGetSymbolAddress with that device current); make that
+ * first call before any stream capture.  Every call reuses the same array,
+ * so calls that overlap on the GPU (other streams or host threads) race:
+ * serialise them.  Errors: STEINER_ENOMEM if n exceeds the limit (nothing
+ * is launched), STEINER_EINVAL (bad sizes, unsorted or out-of-range seeds,
+ * out-of-range neighbour ids), STEINER_EOVERFLOW, STEINER_ETIMEOUT,
+ * STEINER_ECUDA.
+ */
+#define STEINER_NOALLOC_MAX_VERTICES 1048576u
+int steiner_voronoi_noalloc(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,
+                            uint32_t n, uint64_t n_arcs, const int32_t *seeds, uint32_t k,
+                            int32_t *cell, uint32_t *dist, int32_t *pred, void *stream);
+
 /* Release library-allocated outputs. */
 void steiner_result_free(steiner_result_t *r);
 void steiner_pairs_free(steiner_pair_t *pairs);

@@ -79,6 +79,8 @@ SIGNATURES = {
     "steiner_submit": (_i32, [_vp, _vp, _u32, ctypes.POINTER(_u64)]),
     "steiner_poll": (_i32, [_vp, _u64, ctypes.POINTER(steiner_result_t)]),
     "steiner_serve_stop": (_i32, [_vp]),
+    "steiner_voronoi_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u64, _vp, _u32, _vp, _vp, _vp,
+                                       _vp]),
     "steiner_set_param": (_i32, [_vp, ctypes.c_char_p, _i64]),
     "steiner_get_param": (_i64, [_vp, ctypes.c_char_p]),
     "steiner_result_free": (None, [ctypes.POINTER(steiner_result_t)]),
@@ -222,6 +224,21 @@ def steiner_voronoi(h: int, seeds, cell=None, dist=None, pred=None, n: int | Non
     rc = lib.steiner_voronoi(h, s.ctypes.data if s.size else None, s.size, ptr(cell), ptr(dist),
                              ptr(pred))
     return rc, cell, dist, pred
+
+
+def steiner_voronoi_noalloc(row_ptr, col, w, seeds, cell, dist, pred, stream=None) -> int:
+    """Voronoi cells without any device allocation.  Every argument is a
+    CUDA tensor the caller allocated (4-byte elements; seeds sorted
+    ascending); ``stream`` is a torch stream (default: the current one)."""
+    import torch
+    lib = load_library()
+    n = row_ptr.numel() - 1
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+
+    def p(t):
+        return None if t is None else t.data_ptr()
+    return int(lib.steiner_voronoi_noalloc(p(row_ptr), p(col), p(w), n, col.numel(), p(seeds),
+                                           seeds.numel(), p(cell), p(dist), p(pred), st))
 
 
 def steiner_query_batch(h: int, seed_sets) -> tuple[int, list[Result]]:
