@@ -12,7 +12,7 @@ namespace stn {
 // Degree at or above which a vertex's adjacency is processed in chunks of
 // CHUNK arcs (one warp per chunk) instead of inside a 32-vertex batch.
 constexpr uint32_t HEAVY_DEG = 256;
-constexpr uint32_t CHUNK = 1024;
+constexpr uint32_t CHUNK = 512;
 
 // Resident graph: row offsets and interleaved (neighbour, weight) arcs.
 struct DevGraph {

@@ -78,9 +78,14 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const in
 }
 
 // ---------------------------------------------------------------------------
-// relaxation of one arc per lane, with warp-aggregated frontier appends
+// relaxation: U arcs in flight per lane; frontier appends staged per block
 // ---------------------------------------------------------------------------
 
+constexpr int ILP = 4;                 // arcs per lane per round group
+constexpr uint32_t NEAR_STAGE = 2048;  // block staging capacity (near items)
+constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
+
+// Where the appends of one processing segment go.
 struct PushTargets {
     uint32_t *qn;        // light queue of the next iteration
     uint32_t *qn_count;
@@ -94,22 +99,78 @@ struct PushTargets {
     uint64_t T;
 };
 
-// Appends v (a lane's candidate) to the light or heavy near queue.  All
-// lanes of the warp must call it.
-__device__ __forceinline__ void push_near(const SsspArgs &a, const PushTargets &t, bool want,
-                                          uint32_t v) {
-    bool heavy = false;
-    uint32_t nc = 0;
-    if (want) {
-        uint32_t deg = a.row_ptr[v + 1] - a.row_ptr[v];
-        if (deg >= HEAVY_DEG) {
-            heavy = true;
-            nc = (deg + CHUNK - 1) / CHUNK;
-        }
+// Per-block staging buffers: warps append with shared-memory atomics; the
+// block moves them to the global queues with one global atomicAdd each at
+// the end of the segment (flush_stage).  Full buffers spill straight to the
+// global queue.
+struct Stage {
+    uint32_t near_buf[NEAR_STAGE];
+    uint32_t far_buf[FAR_STAGE];
+    uint32_t near_n, far_n, far_min;
+    uint32_t base_near, base_far;
+};
+
+__device__ __forceinline__ void stage_reset(Stage &st) {
+    if (threadIdx.x == 0) {
+        st.near_n = 0;
+        st.far_n = 0;
+        st.far_min = INF32;
     }
-    uint32_t slot = warp_append(want && !heavy, t.qn_count, a.n, &a.ctl->err);
-    if (slot != INF32) t.qn[slot] = v;
+    __syncthreads();
+}
+
+// Warp-aggregated append of v into a staging buffer, spilling to the
+// global queue (gq, gcount, gcap) when the buffer is full.  All lanes call.
+__device__ __forceinline__ void stage_append(bool want, uint32_t v, uint32_t *buf, uint32_t *cnt,
+                                             uint32_t cap, uint32_t *gq, uint32_t *gcount,
+                                             uint32_t gcap, uint32_t *err) {
+    uint32_t mask = __ballot_sync(FULL, want);
+    if (mask == 0) return;
+    uint32_t leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(cnt, (uint32_t)__popc(mask));
+    base = __shfl_sync(FULL, base, leader);
+    uint32_t slot = base + (uint32_t)__popc(mask & lanemask_lt());
+    bool local = want && slot < cap;
+    if (local) buf[slot] = v;
+    uint32_t g = warp_append(want && !local, gcount, gcap, err);
+    if (g != INF32) gq[g] = v;
+}
+
+// Moves the block's staged appends to the global queues.  Called by all
+// threads of the block; ends with the staging buffers still holding data
+// (stage_reset clears them at the next segment).
+__device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uint32_t n,
+                                            uint32_t *err) {
+    __syncthreads();
+    uint32_t nn = min(st.near_n, NEAR_STAGE), nf = min(st.far_n, FAR_STAGE);
+    if (threadIdx.x == 0) {
+        st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
+        st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
+        if (st.far_min != INF32) atomicMin(t.far_min, st.far_min);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        uint32_t slot = st.base_near + i;
+        if (slot < n) t.qn[slot] = st.near_buf[i];
+        else atomicOr(err, ERR_CAPACITY);
+    }
+    for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
+        uint32_t slot = st.base_far + i;
+        if (slot < n) t.farq[slot] = st.far_buf[i];
+        else atomicOr(err, ERR_CAPACITY);
+    }
+}
+
+// Near appends: high-degree vertices become CHUNK-arc items of the heavy
+// queue (per-lane atomics; rare), the rest go through the staging buffer.
+__device__ __forceinline__ void push_near(const SsspArgs &a, Stage &st, const PushTargets &t,
+                                          bool want, uint32_t v, uint32_t deg) {
+    bool heavy = want && deg >= HEAVY_DEG;
+    stage_append(want && !heavy, v, st.near_buf, &st.near_n, NEAR_STAGE, t.qn, t.qn_count, a.n,
+                 &a.ctl->err);
     if (heavy) {
+        uint32_t nc = (deg + CHUNK - 1) / CHUNK;
         uint32_t base = atomicAdd(t.hqn_count, nc);
         if (base + nc > a.heavy_cap) {
             atomicOr(&a.ctl->err, ERR_CAPACITY);
@@ -119,42 +180,68 @@ __device__ __forceinline__ void push_near(const SsspArgs &a, const PushTargets &
     }
 }
 
-__device__ __forceinline__ void relax_arc(const SsspArgs &a, const PushTargets &t, bool valid,
-                                          uint32_t arc, uint64_t du, uint32_t cu,
-                                          unsigned long long &attempts,
-                                          unsigned long long &improved) {
-    bool to_near = false, to_far = false;
-    uint32_t v = 0, nd32 = INF32;
-    if (valid) {
-        uint2 e = __ldg(&a.adj[arc]);
-        v = e.x;
-        uint64_t nd = du + (uint64_t)e.y;
-        ++attempts;
-        if (nd < INF32) {          // a longer proposal is skipped; see the overflow check in the scan
-            uint64_t nl = (nd << 32) | cu;
-            if (nl < ldcg_u64(&a.label[v])) {
-                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[v]),
+__device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const PushTargets &t,
+                                         bool want, uint32_t v, uint32_t d) {
+    stage_append(want, v, st.far_buf, &st.far_n, FAR_STAGE, t.farq, t.far_count, a.n, &a.ctl->err);
+    if (__any_sync(FULL, want)) {
+        uint32_t m = want ? d : INF32;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
+        if (lane_id() == 0 && m != INF32) atomicMin(&st.far_min, m);
+    }
+}
+
+// Relaxes up to ILP arcs per lane.  For arc u of this lane: valid[u], the
+// arc index and the tail's label.  The loads and atomics of the ILP arcs
+// are issued back to back so their latencies overlap.
+__device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const PushTargets &t,
+                                            const bool (&valid)[ILP], const uint32_t (&arc)[ILP],
+                                            const uint64_t (&lab)[ILP],
+                                            unsigned long long &attempts,
+                                            unsigned long long &improved) {
+    uint2 e[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u)
+        if (valid[u]) e[u] = __ldg(&a.adj[arc[u]]);
+    uint64_t nd[ILP];
+    bool imp[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+        imp[u] = false;
+        nd[u] = INF32;
+        if (valid[u]) {
+            ++attempts;
+            nd[u] = (lab[u] >> 32) + (uint64_t)e[u].y;
+            // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
+            if (nd[u] < INF32) {
+                uint64_t nl = (nd[u] << 32) | (lab[u] & 0xFFFFFFFFull);
+                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
                                          (unsigned long long)nl);
-                if (nl < old) {
-                    ++improved;
-                    if (nd < t.T) {
-                        to_near = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
-                    } else {
-                        to_far = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
-                        nd32 = (uint32_t)nd;
-                    }
-                }
+                imp[u] = nl < old;
             }
         }
     }
-    push_near(a, t, to_near, v);
-    uint32_t slot = warp_append(to_far, t.far_count, a.n, &a.ctl->err);
-    if (slot != INF32) t.farq[slot] = v;
-    if (__any_sync(FULL, to_far)) {
-        uint32_t m = nd32;
+    bool to_near[ILP], to_far[ILP];
+    uint32_t deg[ILP];
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
-        if (lane_id() == 0 && m != INF32) atomicMin(t.far_min, m);
+    for (int u = 0; u < ILP; ++u) {
+        to_near[u] = to_far[u] = false;
+        deg[u] = 0;
+        if (!imp[u]) continue;
+        ++improved;
+        uint32_t v = e[u].x;
+        if (nd[u] < t.T) {
+            uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];   // independent of the exchange
+            to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
+            deg[u] = r1 - r0;
+        } else {
+            to_far[u] = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+        push_near(a, st, t, to_near[u], e[u].x, deg[u]);
+        push_far(a, st, t, to_far[u], e[u].x, (uint32_t)nd[u]);
     }
 }
 
@@ -163,6 +250,7 @@ __device__ __forceinline__ void relax_arc(const SsspArgs &a, const PushTargets &
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
+    __shared__ Stage st;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -179,7 +267,14 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
         if (first) {
             ctl->near_count[(it + 2) % 3] = 0;
             ctl->heavy_count[(it + 2) % 3] = 0;
+            if (it < TRACE_LEN) {
+                ctl->trace[it][0] = n_light;
+                ctl->trace[it][1] = n_heavy;
+                ctl->trace[it][2] = ldcg_u32(&ctl->far_count[phase & 1]);
+                ctl->trace[it][3] = (uint32_t)T;
+            }
         }
+        stage_reset(st);
         const bool odd = it & 1;
         const uint32_t *qc = odd ? a.q1 : a.q0;
         const uint64_t *hqc = odd ? a.hq1 : a.hq0;
@@ -196,13 +291,11 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
         t.tag_far = a.base_far + phase;
         t.T = T;
 
-        if (first && it < TRACE_LEN) {
-            ctl->trace[it][0] = n_light;
-            ctl->trace[it][1] = n_heavy;
-            ctl->trace[it][2] = ldcg_u32(&ctl->far_count[phase & 1]);
-            ctl->trace[it][3] = (uint32_t)T;
-        }
-        const uint32_t n_work = n_heavy + (n_light + 31) / 32;
+        // Vertices per warp batch: a thin frontier is spread over all warps
+        // (fewer sequential rounds per warp), a thick one packs 32 per warp.
+        uint32_t per = (n_light + nwarps - 1) / nwarps;
+        uint32_t bsz = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : per <= 8 ? 8 : per <= 16 ? 16 : 32;
+        const uint32_t n_work = n_heavy + (n_light + bsz - 1) / bsz;
         for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
             if (wi < n_heavy) {
                 // one CHUNK of a high-degree vertex per warp
@@ -211,14 +304,22 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
                 uint32_t s = a.row_ptr[u] + c * CHUNK;
                 uint32_t e = min(a.row_ptr[u + 1], s + CHUNK);
                 uint64_t lab = ldcg_u64(&a.label[u]);
-                for (uint32_t b = s; b < e; b += 32) {
-                    uint32_t arc = b + lane;
-                    relax_arc(a, t, arc < e, arc, lab >> 32, (uint32_t)lab, attempts, improved);
+                for (uint32_t b = s; b < e; b += 32 * ILP) {
+                    bool valid[ILP];
+                    uint32_t arc[ILP];
+                    uint64_t labs[ILP];
+#pragma unroll
+                    for (int q = 0; q < ILP; ++q) {
+                        arc[q] = b + lane + 32 * q;
+                        valid[q] = arc[q] < e;
+                        labs[q] = lab;
+                    }
+                    relax_group(a, st, t, valid, arc, labs, attempts, improved);
                 }
             } else {
-                // 32 frontier vertices per warp, their arcs flattened over the lanes
-                uint32_t i = (wi - n_heavy) * 32 + lane;
-                bool has = i < n_light;
+                // bsz frontier vertices per warp, their arcs flattened over the lanes
+                uint32_t i = (wi - n_heavy) * bsz + lane;
+                bool has = lane < bsz && i < n_light;
                 uint32_t s = 0, deg = 0;
                 uint64_t lab = INF64;
                 if (has) {
@@ -231,18 +332,25 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
                 uint32_t incl = warp_inclusive_scan(deg);
                 uint32_t excl = incl - deg;
                 uint32_t total = __shfl_sync(FULL, incl, 31);
-                for (uint32_t b = 0; b < total; b += 32) {
-                    uint32_t j = b + lane;
-                    bool valid = j < total;
-                    uint32_t owner = warp_owner_search(excl, valid ? j : 0);
-                    uint32_t so = __shfl_sync(FULL, s, owner);
-                    uint32_t eo = __shfl_sync(FULL, excl, owner);
-                    uint64_t lo = __shfl_sync(FULL, lab, owner);
-                    relax_arc(a, t, valid, so + (j - eo), lo >> 32, (uint32_t)lo, attempts,
-                              improved);
+                for (uint32_t b = 0; b < total; b += 32 * ILP) {
+                    bool valid[ILP];
+                    uint32_t arc[ILP];
+                    uint64_t labs[ILP];
+#pragma unroll
+                    for (int q = 0; q < ILP; ++q) {
+                        uint32_t j = b + lane + 32 * q;
+                        valid[q] = j < total;
+                        uint32_t owner = warp_owner_search(excl, valid[q] ? j : 0);
+                        uint32_t so = __shfl_sync(FULL, s, owner);
+                        uint32_t eo = __shfl_sync(FULL, excl, owner);
+                        labs[q] = __shfl_sync(FULL, lab, owner);
+                        arc[q] = so + (j - eo);
+                    }
+                    relax_group(a, st, t, valid, arc, labs, attempts, improved);
                 }
             }
         }
+        flush_stage(st, t, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
             if (first) ctl->exit_reason = 3;
             break;
@@ -281,6 +389,7 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
             ctl->near_count[(its + 1) % 3] = 0;
             ctl->heavy_count[(its + 1) % 3] = 0;
         }
+        stage_reset(st);
         PushTargets u;
         u.qn = (its & 1) ? a.q1 : a.q0;
         u.qn_count = &ctl->near_count[its % 3];
@@ -295,7 +404,7 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
         for (uint32_t b = warp * 32; b < nf; b += nwarps * 32) {
             uint32_t i = b + lane;
             bool valid = i < nf;
-            uint32_t v = 0;
+            uint32_t v = 0, deg = 0;
             uint64_t d = INF32;
             if (valid) {
                 v = ldcg_u32(&fs[i]);
@@ -303,16 +412,16 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
             }
             bool to_near = valid && d >= T_old && d < T;     // below T_old: already settled
             bool keep = valid && d >= T;
-            if (to_near) to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
+            if (to_near) {
+                uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
+                to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
+                deg = r1 - r0;
+            }
             if (keep) keep = atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
-            push_near(a, u, to_near, v);
-            uint32_t slot = warp_append(keep, u.far_count, a.n, &ctl->err);
-            if (slot != INF32) u.farq[slot] = v;
-            uint32_t m = keep ? (uint32_t)d : INF32;
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
-            if (lane == 0 && m != INF32) atomicMin(u.far_min, m);
+            push_near(a, st, u, to_near, v, deg);
+            push_far(a, st, u, keep, v, (uint32_t)d);
         }
+        flush_stage(st, u, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
             if (first) ctl->exit_reason = 4;
             break;
@@ -345,7 +454,6 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
         ctl->phases = phase;
     }
 }
-
 // ---------------------------------------------------------------------------
 // export: packed labels -> (cell seed id, distance, predecessor id)
 // ---------------------------------------------------------------------------
