@@ -107,7 +107,7 @@ int ensure_n_workspace(steiner_graph *G) {
     return STEINER_OK;
 }
 
-int ensure_k_workspace(steiner_graph *G, uint32_t k) {
+int ensure_k_workspace(steiner_graph *G, uint32_t k, bool with_pairtab = true) {
     Workspace &ws = G->ws;
     if (k > ws.seeds_cap) {
         CK(dalloc(ws.seeds, k));
@@ -116,7 +116,7 @@ int ensure_k_workspace(steiner_graph *G, uint32_t k) {
     uint64_t slots = k > 1 ? (uint64_t)k * (k - 1) / 2 : 0;
     if (slots > (1ull << 28))
         return fail(STEINER_ENOMEM, "seed set too large for the pair table (k(k-1)/2 > 2^28)");
-    if (slots > ws.pairtab_cap) {
+    if (with_pairtab && slots > ws.pairtab_cap) {
         CK(dalloc(ws.pairtab, slots));
         ws.pairtab_cap = slots;
     }
@@ -466,6 +466,9 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     if (!strcmp(key, "delta")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "delta out of range");
         G->delta = (uint32_t)value;
+    } else if (!strcmp(key, "batch_delta")) {
+        if (value < 0 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "batch_delta out of range");
+        return batch_set_delta(G, (uint32_t)value);
     } else if (!strcmp(key, "max_iters")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "max_iters out of range");
         G->max_iters = (uint32_t)value;
@@ -482,6 +485,7 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "sssp_blocks")) return G->geo.sssp_blocks;
     if (!strcmp(key, "sm_count")) return G->geo.sm_count;
     if (!strcmp(key, "heavy_chunks")) return G->g.n_heavy_chunks;
+    if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);
     return -1;
 }
 
@@ -552,6 +556,50 @@ namespace stn {
 int api_query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_result_t *out) {
     return query_locked(G, seeds, k, out, nullptr, nullptr, nullptr);
 }
+
+// Steps 3-7 of Algorithm 2 for one slot of the multi-query engine: the
+// slot's pair table and strided predecessor column feed the single-query
+// compaction, MST, expansion and sort kernels.  Caller holds G->mu.
+int api_run_tail(steiner_graph *G, uint64_t *pairtab, uint32_t *pred_base, uint32_t pred_stride,
+                 uint32_t k, bool overflow, steiner_result_t *out) {
+    out->edges = nullptr;
+    out->n_edges = 0;
+    out->total = 0;
+    if (overflow)
+        return out->status = fail(STEINER_EOVERFLOW, "a distance or bridge sum reached 2^32 - 1");
+    int rc = ensure_n_workspace(G);
+    if (!rc) rc = ensure_k_workspace(G, k, false);
+    if (rc) return out->status = rc;
+    Workspace v = G->ws;
+    v.pairtab = pairtab;
+    v.pred_arc = pred_base;
+    v.pred_stride = pred_stride;
+    cudaStream_t s = G->stream;
+    CK(cudaMemsetAsync(v.ctl, 0, sizeof(Control), s));
+    CK(launch_compact_pairs(v, k, s));
+    CK(launch_mst(v, k, G->geo, s));
+    CK(launch_tree(G->g, v, k, G->ws.epoch_mark, G->nbits, s));
+    CK(cudaMemcpyAsync(G->h_ctl, v.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    G->ws.epoch_mark += 1;
+    if (G->ws.epoch_mark > 0x7FFFFFFFu) {
+        CK(cudaMemsetAsync(G->ws.mark, 0, (size_t)G->ws.n * 4, s));
+        G->ws.epoch_mark = 1;
+    }
+    const Control c = *G->h_ctl;
+    rc = status_from(c, k, true);
+    if (rc == STEINER_OK || rc == STEINER_EDISCONNECTED) {
+        int rc2 = fetch_tree(G, out);
+        if (rc2) return out->status = rc2;
+    }
+    return out->status = rc;
+}
+
+int api_sorted_seeds(steiner_graph *G, const int32_t *seeds, uint32_t k, std::vector<int32_t> &out) {
+    return sorted_seed_list(G, seeds, k, out);
+}
+
+cudaStream_t api_stream(steiner_graph *G) { return G->stream; }
 
 std::mutex &api_mutex(steiner_graph *G) { return G->mu; }
 const DevGraph &api_graph(steiner_graph *G) { return G->g; }

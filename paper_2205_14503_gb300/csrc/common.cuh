@@ -138,6 +138,24 @@ __device__ __forceinline__ uint32_t warp_append(bool want, uint32_t *count, uint
     return slot;
 }
 
+// Warp-aggregated append of v into a staging buffer, spilling to the
+// global queue (gq, gcount, gcap) when the buffer is full.  All lanes call.
+__device__ __forceinline__ void stage_append(bool want, uint32_t v, uint32_t *buf, uint32_t *cnt,
+                                             uint32_t cap, uint32_t *gq, uint32_t *gcount,
+                                             uint32_t gcap, uint32_t *err) {
+    uint32_t mask = __ballot_sync(FULL, want);
+    if (mask == 0) return;
+    uint32_t leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(cnt, (uint32_t)__popc(mask));
+    base = __shfl_sync(FULL, base, leader);
+    uint32_t slot = base + (uint32_t)__popc(mask & lanemask_lt());
+    bool local = want && slot < cap;
+    if (local) buf[slot] = v;
+    uint32_t g = warp_append(want && !local, gcount, gcap, err);
+    if (g != INF32) gq[g] = v;
+}
+
 // Slot of the seed pair (a, b), a < b < k, in the upper-triangle table:
 // ascending slot order is ascending (a, b) order.
 __host__ __device__ __forceinline__ uint64_t pair_slot(uint64_t a, uint64_t b, uint64_t k) {

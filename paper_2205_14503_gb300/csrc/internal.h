@@ -56,6 +56,7 @@ struct Workspace {
     uint32_t n = 0;
     uint64_t *label = nullptr;      // (dist << 32) | rank
     uint32_t *pred_arc = nullptr;   // arc of the pred edge in v's row; SEED_ARC; INF32
+    uint32_t pred_stride = 1;       // pred of v at pred_arc[v * pred_stride]
     uint32_t *stamp_near = nullptr;
     uint32_t *stamp_far = nullptr;
     uint32_t *mark = nullptr;       // tree-walk stamps

@@ -1,0 +1,783 @@
+// Multi-query Voronoi cells and bridge scan (the batched and serving modes).
+//
+// The arithmetic per query is exactly the single-query path's (Algorithm 2
+// Steps 1-2 with the same packed (distance, rank) atomicMin fixed point and
+// the same tie rules); what changes is how the work of up to 64 queries is
+// shared:
+//  * labels are vertex-major, label[v * 64 + q], so relaxing one arc for all
+//    pending slots is one contiguous 512-byte run of atomics;
+//  * a frontier entry is a vertex; nmask[v] says which slots must relax
+//    v's arcs, so a CSR row is read once for all of them;
+//  * each slot has its own near/far threshold T[q] and far accounting, so a
+//    slot admitted mid-run starts its own bands (continuous batching);
+//  * the persistent kernel can yield at an iteration boundary (a slot
+//    converged, or the host rang the doorbell), keeping all state in device
+//    memory, and resume later with more slots.
+#include "multi.h"
+
+namespace stn {
+
+constexpr int MQ_ILP = 4;
+constexpr uint32_t MQ_NEAR_STAGE = 1024;
+constexpr uint32_t MQ_FAR_STAGE = 512;
+
+struct MqArgs {
+    const uint32_t *__restrict__ row_ptr;
+    const uint2 *__restrict__ adj;
+    uint32_t n;
+    uint64_t *label;
+    unsigned long long *nmask, *fmask;
+    uint32_t *stamp_near, *in_far;
+    uint32_t *q0, *q1;
+    unsigned long long *item_mask;   // per frontier item: the slots it relaxes
+    uint64_t *item_pre;              // per item: (arc, slot) pairs before it in its block segment
+    uint64_t *bsum;                  // per block: pairs in its segment
+    uint32_t *far0, *far1;
+    MqControl *ctl;
+    const uint32_t *doorbell;
+    uint32_t delta;
+    uint32_t base_near;
+    uint32_t max_iters;
+    uint32_t yield;
+};
+
+constexpr int MQ_WARPS = 256 / 32;
+constexpr int MQ_MAX_BLOCKS = 1024;
+
+struct MqStage {
+    uint64_t boff[MQ_MAX_BLOCKS];          // pair offset of each block's frontier segment
+    uint64_t wtot[MQ_WARPS];
+    uint64_t carry, W;
+    uint32_t near_buf[MQ_NEAR_STAGE];
+    uint32_t far_buf[MQ_FAR_STAGE];
+    uint32_t near_n, far_n, base_near, base_far;
+    unsigned long long act;
+    unsigned long long T[MQ_SLOTS];        // current thresholds (block copy)
+    unsigned long long Tnew[MQ_SLOTS];     // thresholds after a split
+    uint32_t fmin[MQ_SLOTS];               // far-distance minimum of this segment
+    int32_t fpend[MQ_SLOTS];               // change of far_pending in this segment
+};
+
+struct MqTargets {
+    uint32_t *qn, *qn_count;
+    unsigned long long *act;
+    uint32_t *farq, *far_count;
+    uint32_t *fmin;          // ctl->fmin[pile]
+    uint32_t tag_next;
+};
+
+__device__ __forceinline__ int popc64(unsigned long long x) { return __popcll(x); }
+
+// Inclusive scan of one 64-bit value per thread over a 256-thread block;
+// wtot[] receives the per-warp inclusive totals (wtot[MQ_WARPS-1] = block
+// total after the call).  Every thread of the block must call it.
+__device__ __forceinline__ uint64_t block_inclusive_scan64(uint64_t x, uint64_t *wtot) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) wtot[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t acc = 0;
+        for (int i = 0; i < MQ_WARPS; ++i) {
+            acc += wtot[i];
+            wtot[i] = acc;
+        }
+    }
+    __syncthreads();
+    return x + (w ? wtot[w - 1] : 0);
+}
+
+// Index of the t-th set bit (0-based) of a 32-bit word.
+__device__ __forceinline__ uint32_t nth_bit32(uint32_t x, uint32_t t) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t w = 16; w >= 1; w >>= 1) {
+        uint32_t c = __popc(x & ((1u << w) - 1u));
+        if (t >= c) {
+            t -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+__device__ __forceinline__ uint32_t nth_bit64(unsigned long long m, uint32_t t) {
+    uint32_t lo = (uint32_t)m, pl = (uint32_t)__popc(lo);
+    return t < pl ? nth_bit32(lo, t) : 32 + nth_bit32((uint32_t)(m >> 32), t - pl);
+}
+
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
+    uint32_t lo = __reduce_or_sync(FULL, (uint32_t)x);
+    uint32_t hi = __reduce_or_sync(FULL, (uint32_t)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ void seg_reset(MqStage &st) {
+    if (threadIdx.x == 0) {
+        st.near_n = 0;
+        st.far_n = 0;
+        st.act = 0;
+    }
+    if (threadIdx.x < MQ_SLOTS) {
+        st.fmin[threadIdx.x] = INF32;
+        st.fpend[threadIdx.x] = 0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void seg_flush(MqStage &st, const MqTargets &t, MqControl *ctl,
+                                          uint32_t n) {
+    __syncthreads();
+    uint32_t nn = min(st.near_n, MQ_NEAR_STAGE), nf = min(st.far_n, MQ_FAR_STAGE);
+    if (threadIdx.x == 0) {
+        st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
+        st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
+        if (st.act) atomicOr(t.act, st.act);
+    }
+    if (threadIdx.x < MQ_SLOTS) {
+        uint32_t q = threadIdx.x;
+        if (st.fmin[q] != INF32) atomicMin(&t.fmin[q], st.fmin[q]);
+        if (st.fpend[q]) atomicAdd(&ctl->far_pending[q], st.fpend[q]);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        uint32_t slot = st.base_near + i;
+        if (slot < n) t.qn[slot] = st.near_buf[i];
+        else atomicOr(&ctl->err, ERR_CAPACITY);
+    }
+    for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
+        uint32_t slot = st.base_far + i;
+        if (slot < n) t.farq[slot] = st.far_buf[i];
+        else atomicOr(&ctl->err, ERR_CAPACITY);
+    }
+}
+
+// A vertex with near work joins the next frontier through the staging
+// buffer.  (Hubs need no special handling: work is split by pairs.)
+__device__ __forceinline__ void mq_push_near(const MqArgs &a, MqStage &st, const MqTargets &t,
+                                             bool want, uint32_t v) {
+    stage_append(want, v, st.near_buf, &st.near_n, MQ_NEAR_STAGE, t.qn, t.qn_count, a.n,
+                 &a.ctl->err);
+}
+
+// Relaxes up to MQ_ILP (arc, slot) pairs per lane.
+__device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqTargets &t,
+                                         const bool (&valid)[MQ_ILP],
+                                         const uint32_t (&arc)[MQ_ILP],
+                                         const uint32_t (&qs)[MQ_ILP],
+                                         const uint64_t (&lab)[MQ_ILP],
+                                         unsigned long long &attempts,
+                                         unsigned long long &improved) {
+    uint2 e[MQ_ILP];
+#pragma unroll
+    for (int i = 0; i < MQ_ILP; ++i)
+        if (valid[i]) e[i] = __ldg(&a.adj[arc[i]]);
+    uint64_t nd[MQ_ILP];
+    bool imp[MQ_ILP];
+#pragma unroll
+    for (int i = 0; i < MQ_ILP; ++i) {
+        imp[i] = false;
+        nd[i] = INF32;
+        if (!valid[i] || lab[i] == INF64) continue;
+        ++attempts;
+        nd[i] = (lab[i] >> 32) + (uint64_t)e[i].y;
+        if (nd[i] < INF32) {
+            // read first: most proposals do not improve, and a load costs far
+            // less L2 throughput than an atomic
+            uint64_t nl = (nd[i] << 32) | (lab[i] & 0xFFFFFFFFull);
+            uint64_t *dst = &a.label[(uint64_t)e[i].x * MQ_SLOTS + qs[i]];
+            if (nl < ldcg_u64(dst)) {
+                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(dst),
+                                         (unsigned long long)nl);
+                imp[i] = nl < old;
+            }
+        }
+    }
+    bool to_near[MQ_ILP], to_far[MQ_ILP];
+    unsigned long long act = 0;
+#pragma unroll
+    for (int i = 0; i < MQ_ILP; ++i) {
+        to_near[i] = to_far[i] = false;
+        if (!imp[i]) continue;
+        ++improved;
+        uint32_t v = e[i].x, q = qs[i];
+        unsigned long long bit = 1ull << q;
+        if (nd[i] < st.T[q]) {
+            atomicOr(&a.nmask[v], bit);
+            to_near[i] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
+            act |= bit;
+        } else {
+            unsigned long long old = atomicOr(&a.fmask[v], bit);
+            if (!(old & bit)) atomicAdd(&st.fpend[q], 1);
+            atomicMin(&st.fmin[q], (uint32_t)nd[i]);
+            to_far[i] = atomicExch(&a.in_far[v], 1u) == 0;
+        }
+    }
+    act = warp_or64(act);
+    if (lane_id() == 0 && act) atomicOr(&st.act, act);
+#pragma unroll
+    for (int i = 0; i < MQ_ILP; ++i) {
+        mq_push_near(a, st, t, to_near[i], e[i].x);
+        stage_append(to_far[i], e[i].x, st.far_buf, &st.far_n, MQ_FAR_STAGE, t.farq, t.far_count,
+                     a.n, &a.ctl->err);
+    }
+}
+
+__global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
+    __shared__ MqStage st;
+    MqControl *ctl = a.ctl;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gthreads = gridDim.x * blockDim.x;
+    const bool first = gtid == 0;
+    unsigned long long attempts = 0, improved = 0;
+    uint32_t it = ldcg_u32(&ctl->it), fc = ldcg_u32(&ctl->fc);
+    unsigned long long infl = __ldcg(&ctl->inflight) & ~__ldcg(&ctl->converged);
+    unsigned long long conv_total = 0;
+    if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
+    __syncthreads();
+    uint32_t iters = 0, reason = 0;
+
+    while (infl) {
+        const uint32_t cs = it % 3, ns = (it + 1) % 3;
+        const bool odd = it & 1;
+        const uint32_t n_items = min(ldcg_u32(&ctl->near_count[cs]), a.n);
+        if (first) {
+            uint32_t r = (it + 2) % 3;
+            ctl->near_count[r] = 0;
+            ctl->act[r] = 0;
+        }
+        const uint32_t *qc = odd ? a.q1 : a.q0;
+
+        // Phase A: every frontier vertex takes its pending slot mask; its
+        // work is deg x |mask| (arc, slot) pairs; prefix sums per block
+        // segment of the frontier.
+        const uint32_t seg = (n_items + gridDim.x - 1) / gridDim.x;
+        const uint32_t seg_lo = min(n_items, blockIdx.x * seg);
+        const uint32_t seg_hi = min(n_items, seg_lo + seg);
+        if (threadIdx.x == 0) st.carry = 0;
+        __syncthreads();
+        for (uint32_t b0 = seg_lo; b0 < seg_hi; b0 += blockDim.x) {
+            uint32_t i = b0 + threadIdx.x;
+            uint64_t w = 0;
+            if (i < seg_hi) {
+                uint32_t u = ldcg_u32(&qc[i]);
+                unsigned long long M = atomicExch(&a.nmask[u], 0ull);
+                a.item_mask[i] = M;
+                w = (uint64_t)(a.row_ptr[u + 1] - a.row_ptr[u]) * (uint64_t)popc64(M);
+            }
+            uint64_t incl = block_inclusive_scan64(w, st.wtot);
+            if (i < seg_hi) a.item_pre[i] = st.carry + incl - w;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) st.carry += incl;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.bsum[blockIdx.x] = st.carry;
+        if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        // block offsets and the total
+        {
+            uint64_t carry = 0;
+            for (uint32_t b0 = 0; b0 < gridDim.x; b0 += blockDim.x) {
+                uint32_t b = b0 + threadIdx.x;
+                uint64_t x = b < gridDim.x ? __ldcg(reinterpret_cast<const unsigned long long *>(&a.bsum[b])) : 0;
+                uint64_t incl = block_inclusive_scan64(x, st.wtot);
+                if (b < gridDim.x) st.boff[b] = carry + incl - x;
+                __syncthreads();
+                carry += st.wtot[MQ_WARPS - 1];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) st.W = carry;
+            __syncthreads();
+        }
+        seg_reset(st);
+        MqTargets t;
+        t.qn = odd ? a.q0 : a.q1;
+        t.qn_count = &ctl->near_count[ns];
+        t.act = &ctl->act[ns];
+        t.farq = fc ? a.far1 : a.far0;
+        t.far_count = &ctl->far_count[fc];
+        t.fmin = ctl->fmin[fc];
+        t.tag_next = a.base_near + it + 1;
+
+        // Phase B: warp w relaxes pairs [W w / nw, W (w + 1) / nw).  Pairs of
+        // an item are numbered arc-major (arc j, slot t -> j * |mask| + t).
+        // Lanes are grouped by the item's slot count: a group of g lanes
+        // (g = |mask| rounded up to a power of two, at most 32) takes one arc,
+        // lane t of the group its t-th slot, so a warp relaxes 32 / g arcs per
+        // round with one broadcast arc load per group and the tail's label
+        // for that slot held in a register for the whole item.
+        const uint64_t W = st.W;
+        uint64_t p = (uint64_t)((unsigned __int128)W * warp / nwarps);
+        const uint64_t p1 = (uint64_t)((unsigned __int128)W * (warp + 1) / nwarps);
+        if (p < p1) {
+            auto gpre = [&](uint32_t i) -> uint64_t {
+                return st.boff[i / seg] + __ldcg(reinterpret_cast<const unsigned long long *>(&a.item_pre[i]));
+            };
+            uint32_t lo = 0, hi = n_items;          // first item: largest i with gpre(i) <= p
+            while (hi - lo > 1) {
+                uint32_t mid = lo + (hi - lo) / 2;
+                if (gpre(mid) <= p) lo = mid; else hi = mid;
+            }
+            for (uint32_t i = lo; i < n_items && p < p1; ++i) {
+                const uint64_t base = gpre(i);
+                const uint32_t u = ldcg_u32(&qc[i]);
+                const unsigned long long M = __ldcg(&a.item_mask[i]);
+                const uint32_t c = (uint32_t)popc64(M);
+                if (c == 0) continue;
+                const uint32_t s0 = a.row_ptr[u], deg = a.row_ptr[u + 1] - s0;
+                const uint64_t iend = base + (uint64_t)deg * c;
+                if (iend <= p) continue;
+                // arcs of this item that hold pairs in [p, p1)
+                const uint64_t lo_p = p > base ? p - base : 0;
+                const uint64_t hi_p = min(p1, iend) - base;
+                const uint32_t ja = (uint32_t)(lo_p / c), jb = (uint32_t)((hi_p + c - 1) / c);
+                const uint32_t g = c >= 32 ? 32 : (c > 16 ? 32 : c > 8 ? 16 : c > 4 ? 8 : c > 2 ? 4 : c);
+                const uint32_t gsh = g == 32 ? 5 : g == 16 ? 4 : g == 8 ? 3 : g == 4 ? 2 : g == 2 ? 1 : 0;
+                const uint32_t apr = 32 >> gsh;               // arcs per round
+                const uint32_t grp = lane >> gsh, tl = lane & (g - 1);
+                for (uint32_t pass = 0; pass * 32 < c; ++pass) {   // slots t and t + 32
+                    const uint32_t ts = tl + pass * 32;
+                    const bool has_slot = ts < c;
+                    const uint32_t q = has_slot ? nth_bit64(M, ts) : 0;
+                    const uint64_t lu = has_slot ? ldcg_u64(&a.label[(uint64_t)u * MQ_SLOTS + q]) : INF64;
+                    for (uint32_t j0 = ja; j0 < jb; j0 += apr * MQ_ILP) {
+                        bool valid[MQ_ILP];
+                        uint32_t arc[MQ_ILP], qs[MQ_ILP];
+                        uint64_t labs[MQ_ILP];
+#pragma unroll
+                        for (int k = 0; k < MQ_ILP; ++k) {
+                            uint32_t j = j0 + k * apr + grp;
+                            uint64_t pidx = (uint64_t)j * c + ts;    // pair index within the item
+                            valid[k] = has_slot && j < jb && pidx >= lo_p && pidx < hi_p;
+                            arc[k] = s0 + j;
+                            qs[k] = q;
+                            labs[k] = lu;
+                        }
+                        mq_relax(a, st, t, valid, arc, qs, labs, attempts, improved);
+                    }
+                }
+                p = iend;
+            }
+        }
+        seg_flush(st, t, ctl, a.n);
+        if (first) ctl->stop_req = (a.yield && a.doorbell) ? *(volatile const uint32_t *)a.doorbell : 0u;
+        if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        ++it;
+        ++iters;
+
+        // per-slot decisions (every block computes the same from global state)
+        unsigned long long act_next = __ldcg(&ctl->act[it % 3]);
+        unsigned long long idle = infl & ~act_next, S = 0, conv = 0;
+        for (unsigned long long m = idle; m; m &= m - 1) {
+            uint32_t q = __ffsll((long long)m) - 1;
+            if (__ldcg(&ctl->far_pending[q]) <= 0) conv |= 1ull << q;
+            else S |= 1ull << q;
+        }
+        infl &= ~conv;
+        conv_total |= conv;
+        if (!infl) { reason = 1; break; }
+        if (a.yield && conv_total) { reason = 2; break; }
+        if (a.yield && ldcg_u32(&ctl->stop_req)) { reason = 3; break; }
+        if (iters >= a.max_iters) { reason = 4; break; }
+        if (!S) continue;
+
+        // Split the far pile for the slots in S.  A barrier first: every
+        // block has read the decision inputs before the split appends to
+        // them.  Near pushes go to this iteration's queue (slot it % 3).
+        if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        if (threadIdx.x < MQ_SLOTS) {
+            uint32_t q = threadIdx.x;
+            unsigned long long Tq = st.T[q];
+            if ((S >> q) & 1) {
+                uint32_t fm = __ldcg(&ctl->fmin[fc][q]);
+                unsigned long long base = (fm != INF32 && (unsigned long long)fm > Tq) ? fm : Tq;
+                st.Tnew[q] = base + a.delta;
+            } else {
+                st.Tnew[q] = Tq;
+            }
+        }
+        seg_reset(st);
+        const bool odd2 = it & 1;
+        MqTargets u;
+        u.qn = odd2 ? a.q1 : a.q0;
+        u.qn_count = &ctl->near_count[it % 3];
+        u.act = &ctl->act[it % 3];
+        u.farq = fc ? a.far0 : a.far1;
+        u.far_count = &ctl->far_count[fc ^ 1];
+        u.fmin = ctl->fmin[fc ^ 1];
+        u.tag_next = a.base_near + it;
+        const uint32_t *fs = fc ? a.far1 : a.far0;
+        const uint32_t nf = min(ldcg_u32(&ctl->far_count[fc]), a.n);
+        for (uint32_t b = warp * 32; b < nf; b += nwarps * 32) {
+            uint32_t i = b + lane;
+            bool valid = i < nf;
+            uint32_t v = valid ? ldcg_u32(&fs[i]) : 0;
+            unsigned long long M = valid ? __ldcg(&a.fmask[v]) : 0ull;
+            unsigned long long MS = M & S, moved = 0, dropped = 0;
+            for (unsigned long long m = MS; m; m &= m - 1) {
+                uint32_t q = __ffsll((long long)m) - 1;
+                uint64_t d = ldcg_u64(&a.label[(uint64_t)v * MQ_SLOTS + q]) >> 32;
+                if (d < st.T[q]) {
+                    dropped |= 1ull << q;                  // settled while parked
+                } else if (d < st.Tnew[q]) {
+                    moved |= 1ull << q;
+                } else {
+                    atomicMin(&st.fmin[q], (uint32_t)d);
+                }
+            }
+            unsigned long long cleared = moved | dropped;
+            if (cleared) {
+                atomicAnd(&a.fmask[v], ~cleared);
+                for (unsigned long long m = cleared; m; m &= m - 1)
+                    atomicSub(&st.fpend[__ffsll((long long)m) - 1], 1);
+            }
+            bool to_near = false;
+            if (moved) {
+                atomicOr(&a.nmask[v], moved);
+                to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
+            }
+            unsigned long long act = warp_or64(moved);
+            if (lane == 0 && act) atomicOr(&st.act, act);
+            bool keep = valid && (M & ~cleared) != 0;
+            if (valid && !keep) a.in_far[v] = 0;
+            mq_push_near(a, st, u, to_near, v);
+            stage_append(keep, v, st.far_buf, &st.far_n, MQ_FAR_STAGE, u.farq, u.far_count, a.n,
+                         &ctl->err);
+        }
+        seg_flush(st, u, ctl, a.n);
+        if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        if (first) {
+            for (uint32_t q = 0; q < MQ_SLOTS; ++q) {
+                if (!((S >> q) & 1)) {
+                    uint32_t fm = ctl->fmin[fc][q];
+                    if (fm != INF32) atomicMin(&ctl->fmin[fc ^ 1][q], fm);
+                }
+                ctl->fmin[fc][q] = INF32;
+            }
+            ctl->far_count[fc] = 0;
+        }
+        if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = st.Tnew[threadIdx.x];
+        __syncthreads();
+        fc ^= 1;
+    }
+    if (!infl && reason == 0) reason = 1;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        attempts += __shfl_xor_sync(FULL, attempts, o);
+        improved += __shfl_xor_sync(FULL, improved, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&ctl->relax_attempts, attempts);
+        atomicAdd(&ctl->relax_improved, improved);
+    }
+    if (first) {
+        ctl->it = it;
+        ctl->fc = fc;
+        ctl->converged |= conv_total;
+        ctl->iterations = iters;
+        ctl->exit_reason = reason;
+        for (uint32_t q = 0; q < MQ_SLOTS; ++q) ctl->T[q] = st.T[q];
+        if (reason == 4 && infl) atomicOr(&ctl->err, 0u);   // a capped launch resumes later
+    }
+}
+
+// ---------------------------------------------------------------------------
+// admission of one slot: clear its label/pred column, seed it
+// ---------------------------------------------------------------------------
+
+__global__ void mq_clear_column_kernel(uint32_t n, uint64_t *label, uint32_t *pred, uint32_t q) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        label[(uint64_t)v * MQ_SLOTS + q] = INF64;
+        pred[(uint64_t)v * MQ_SLOTS + q] = INF32;
+    }
+}
+
+// Clears the label/pred columns of every slot in `mask` with row-wide,
+// coalesced stores (one thread per (vertex, slot) element).
+__global__ void mq_clear_rows_kernel(uint32_t n, uint64_t *label, uint32_t *pred,
+                                     unsigned long long mask) {
+    uint64_t total = (uint64_t)n * MQ_SLOTS;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if ((mask >> (i & (MQ_SLOTS - 1))) & 1ull) {
+            label[i] = INF64;
+            pred[i] = INF32;
+        }
+    }
+}
+
+__global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n, const int32_t *seeds,
+                               uint32_t k, uint32_t q, uint32_t delta, MqState m) {
+    MqControl *ctl = m.ctl;
+    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t it = ctl->it;
+    const unsigned long long bit = 1ull << q;
+    if (r == 0) {
+        ctl->T[q] = delta;
+        ctl->fmin[0][q] = INF32;
+        ctl->fmin[1][q] = INF32;
+        ctl->far_pending[q] = 0;
+        atomicOr(&ctl->act[it % 3], bit);
+        ctl->slot_overflow &= ~bit;
+    }
+    if (r >= k) return;
+    uint32_t s = (uint32_t)seeds[r];
+    m.label[(uint64_t)s * MQ_SLOTS + q] = (uint64_t)r;
+    m.pred[(uint64_t)s * MQ_SLOTS + q] = SEED_ARC;
+    atomicOr(&m.nmask[s], bit);
+    uint32_t tag = m.base_near + it;
+    if (atomicExch(&m.stamp_near[s], tag) == tag) return;   // already queued for iteration it
+    uint32_t slot = atomicAdd(&ctl->near_count[it % 3], 1u);
+    if (slot >= n) {
+        atomicOr(&ctl->err, ERR_CAPACITY);
+        return;
+    }
+    ((it & 1) ? m.q[1] : m.q[0])[slot] = s;
+}
+
+// ---------------------------------------------------------------------------
+// batched pred + bridge scan for a set of converged slots
+// ---------------------------------------------------------------------------
+
+struct MqScanArgs {
+    const uint32_t *__restrict__ row_ptr;
+    const uint2 *__restrict__ adj;
+    const uint64_t *__restrict__ heavy_chunks;
+    uint32_t n_heavy_chunks;
+    uint32_t n;
+    const uint64_t *label;
+    uint32_t *pred;
+    uint64_t *const *pairtab;
+    const uint32_t *k;
+    unsigned long long slots;
+    MqControl *ctl;
+};
+
+__device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, uint32_t v,
+                                             uint32_t arc, uint32_t q,
+                                             unsigned long long &overflow) {
+    if (!valid) return;
+    uint2 e = __ldg(&a.adj[arc]);
+    uint64_t lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)v * MQ_SLOTS + q]));
+    uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + q]));
+    if (lv == INF64 || lu == INF64) {
+        if (lv != lu) overflow |= 1ull << q;
+        return;
+    }
+    uint32_t cv = (uint32_t)lv, cu = (uint32_t)lu;
+    uint64_t dv = lv >> 32, du = lu >> 32;
+    if (cu == cv) {
+        if (du + e.y == dv) atomicMin(&a.pred[(uint64_t)v * MQ_SLOTS + q], arc);
+    } else if (cv < cu) {
+        uint64_t b = dv + e.y + du;
+        if (b >= INF32) {
+            overflow |= 1ull << q;
+            return;
+        }
+        uint64_t key = (b << 32) | arc;
+        uint64_t *slot = &a.pairtab[q][pair_slot(cv, cu, a.k[q])];
+        if (key < ldcg_u64(slot))
+            atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
+    }
+}
+
+// One vertex's arcs [s0, s1) for every slot of the launch.  Lanes are
+// grouped as in the SSSP kernel: a group of g lanes takes one arc, lane t of
+// the group the t-th slot (t + 32 on a second pass when over 32 slots).
+__device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uint32_t s0,
+                                            uint32_t s1, uint32_t cnt, uint32_t gsh,
+                                            unsigned long long &overflow) {
+    const uint32_t lane = lane_id();
+    const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh, tl = lane & (g - 1);
+    for (uint32_t pass = 0; pass * 32 < cnt; ++pass) {
+        const uint32_t ts = tl + pass * 32;
+        const bool has_slot = ts < cnt;
+        const uint32_t q = has_slot ? nth_bit64(a.slots, ts) : 0;
+        for (uint32_t j0 = s0; j0 < s1; j0 += apr * 4) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t arc = j0 + k * apr + grp;
+                mq_scan_pair(a, has_slot && arc < s1, v, arc, q, overflow);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t cnt = (uint32_t)popc64(a.slots);
+    const uint32_t gsh = cnt > 16 ? 5 : cnt > 8 ? 4 : cnt > 4 ? 3 : cnt > 2 ? 2 : cnt > 1 ? 1 : 0;
+    const uint32_t n_batches = (a.n + 31) / 32;
+    const uint32_t n_work = a.n_heavy_chunks + n_batches;
+    unsigned long long overflow = 0;
+    for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
+        if (wi < a.n_heavy_chunks) {
+            uint64_t item = a.heavy_chunks[wi];
+            uint32_t v = (uint32_t)(item >> 32), c = (uint32_t)item;
+            uint32_t s = a.row_ptr[v] + c * CHUNK;
+            uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
+            mq_scan_row(a, v, s, e, cnt, gsh, overflow);
+        } else {
+            uint32_t v0 = (wi - a.n_heavy_chunks) * 32;
+            uint32_t vl = v0 + lane;
+            uint32_t rs = vl < a.n ? a.row_ptr[vl] : 0;
+            uint32_t re = vl < a.n ? a.row_ptr[vl + 1] : 0;
+            for (uint32_t l = 0; l < 32 && v0 + l < a.n; ++l) {
+                uint32_t s = __shfl_sync(FULL, rs, l), e = __shfl_sync(FULL, re, l);
+                if (e - s >= HEAVY_DEG) continue;          // covered by the chunk list
+                mq_scan_row(a, v0 + l, s, e, cnt, gsh, overflow);
+            }
+        }
+    }
+    overflow = warp_or64(overflow);
+    if (lane == 0 && overflow) atomicOr(&a.ctl->slot_overflow, overflow);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <class T>
+static cudaError_t mq_dalloc(T *&p, uint64_t count) {
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)&p, count * sizeof(T));
+}
+
+cudaError_t mq_alloc(const DevGraph &g, MqState &m, cudaStream_t s) {
+    uint32_t n = g.n;
+    m.n = n;
+    cudaError_t e;
+#define MA(ptr, cnt) if ((e = mq_dalloc(ptr, cnt)) != cudaSuccess) return e
+    MA(m.label, (uint64_t)n * MQ_SLOTS);
+    MA(m.pred, (uint64_t)n * MQ_SLOTS);
+    MA(m.nmask, n);
+    MA(m.fmask, n);
+    MA(m.stamp_near, n);
+    MA(m.in_far, n);
+    for (int i = 0; i < 2; ++i) {
+        MA(m.q[i], n);
+        MA(m.far[i], n);
+    }
+    MA(m.item_mask, n);
+    MA(m.item_pre, n);
+    MA(m.bsum, MQ_MAX_BLOCKS);
+    MA(m.ctl, 1);
+    MA(m.d_pairtab, MQ_SLOTS);
+    MA(m.d_k, MQ_SLOTS);
+#undef MA
+    if ((e = cudaMemsetAsync(m.nmask, 0, (size_t)n * 8, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.fmask, 0, (size_t)n * 8, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.stamp_near, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.in_far, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.ctl, 0, sizeof(MqControl), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.d_pairtab, 0, MQ_SLOTS * sizeof(uint64_t *), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.d_k, 0, MQ_SLOTS * 4, s)) != cudaSuccess) return e;
+    m.base_near = 1;
+    return cudaSuccess;
+}
+
+void mq_free(MqState &m) {
+    void *bufs[] = {m.label, m.pred, m.nmask, m.fmask, m.stamp_near, m.in_far, m.q[0], m.q[1],
+                    m.item_mask, m.item_pre, m.bsum, m.far[0], m.far[1], m.ctl, m.d_pairtab,
+                    m.d_k};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    for (int q = 0; q < MQ_SLOTS; ++q) {
+        if (m.pairtab[q]) cudaFree(m.pairtab[q]);
+        if (m.seeds[q]) cudaFree(m.seeds[q]);
+    }
+    m = MqState();
+}
+
+int mq_occupancy(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mq_sssp_kernel, threads, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t mq_launch_clear(const DevGraph &g, MqState &m, unsigned long long mask,
+                            cudaStream_t s) {
+    if (!mask) return cudaSuccess;
+    if (__builtin_popcountll(mask) >= 8) {
+        mq_clear_rows_kernel<<<152 * 16, 256, 0, s>>>(g.n, m.label, m.pred, mask);
+    } else {
+        unsigned grid = (unsigned)std::min<uint64_t>((g.n + 255) / 256, 152ull * 16);
+        for (unsigned long long mm = mask; mm; mm &= mm - 1)
+            mq_clear_column_kernel<<<grid, 256, 0, s>>>(g.n, m.label, m.pred,
+                                                        (uint32_t)__builtin_ctzll(mm));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uint32_t delta,
+                           cudaStream_t s) {
+    mq_seed_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, g.n, m.seeds[q], k, (uint32_t)q,
+                                                    delta, m);
+    return cudaGetLastError();
+}
+
+cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
+                           uint32_t max_iters, bool yield, const uint32_t *doorbell,
+                           cudaStream_t s) {
+    MqArgs a;
+    a.row_ptr = g.row_ptr;
+    a.adj = g.adj;
+    a.n = g.n;
+    a.label = m.label;
+    a.nmask = m.nmask;
+    a.fmask = m.fmask;
+    a.stamp_near = m.stamp_near;
+    a.in_far = m.in_far;
+    a.q0 = m.q[0];
+    a.q1 = m.q[1];
+    a.item_mask = m.item_mask;
+    a.item_pre = m.item_pre;
+    a.bsum = m.bsum;
+    a.far0 = m.far[0];
+    a.far1 = m.far[1];
+    a.ctl = m.ctl;
+    a.doorbell = doorbell;
+    a.delta = delta;
+    a.base_near = m.base_near;
+    a.max_iters = max_iters;
+    a.yield = yield ? 1u : 0u;
+    cudaError_t e = cudaMemsetAsync(&m.ctl->bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    if (blocks > MQ_MAX_BLOCKS) blocks = MQ_MAX_BLOCKS;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)mq_sssp_kernel, dim3(blocks), dim3(256), args,
+                                       0, s);
+}
+
+cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slots,
+                           cudaStream_t s) {
+    if (!slots) return cudaSuccess;
+    MqScanArgs a;
+    a.row_ptr = g.row_ptr;
+    a.adj = g.adj;
+    a.heavy_chunks = g.heavy_chunks;
+    a.n_heavy_chunks = g.n_heavy_chunks;
+    a.n = g.n;
+    a.label = m.label;
+    a.pred = m.pred;
+    a.pairtab = m.d_pairtab;
+    a.k = m.d_k;
+    a.slots = slots;
+    a.ctl = m.ctl;
+    uint64_t work = (uint64_t)g.n_heavy_chunks + (g.n + 31) / 32;
+    uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + 7) / 8, 152ull * 32));
+    mq_scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace stn

@@ -1,0 +1,83 @@
+// Multi-query engine state shared by the batch and serving entry points.
+//
+// Up to MQ_SLOTS queries ("slots") run in one persistent kernel over the
+// resident graph.  Per-vertex state is vertex-major: the labels of vertex v
+// for all slots are label[v * MQ_SLOTS + q], so relaxing one arc for every
+// pending slot touches one contiguous 512-byte run, and each CSR row is
+// read once per frontier visit for all the slots that need it (a 64-bit
+// mask per vertex says which).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace stn {
+
+constexpr int MQ_SLOTS = 64;
+
+struct MqControl {
+    GridBarrier bar;
+    uint32_t err;                 // ERR_* (global)
+    uint32_t it;                  // next iteration (persists across launches)
+    uint32_t fc;                  // far pile being filled
+    uint32_t stop_req;            // published by block 0 before each barrier
+    uint32_t near_count[3];
+    uint32_t far_count[2];
+    unsigned long long act[3];    // slots with near work queued, per iteration slot
+    unsigned long long inflight;  // admitted, not yet converged (host-written)
+    unsigned long long converged; // converged slots (kernel-written, host clears)
+    unsigned long long slot_overflow;   // per-slot overflow seen by the scan
+    unsigned long long T[MQ_SLOTS];     // near/far threshold per slot
+    uint32_t fmin[2][MQ_SLOTS];         // lower bound of far distances per slot
+    int32_t far_pending[MQ_SLOTS];      // set far bits per slot
+    uint32_t exit_reason;               // 1 all converged, 2 slot converged, 3 yield, 4 cap, 5 barrier
+    uint32_t iterations;                // iterations run by the last launch
+    unsigned long long relax_attempts;
+    unsigned long long relax_improved;
+};
+
+struct MqState {
+    uint32_t n = 0;
+    uint64_t *label = nullptr;              // n * MQ_SLOTS
+    uint32_t *pred = nullptr;               // n * MQ_SLOTS (pred arc per slot)
+    unsigned long long *nmask = nullptr;    // n
+    unsigned long long *fmask = nullptr;    // n
+    uint32_t *stamp_near = nullptr;         // n
+    uint32_t *in_far = nullptr;             // n
+    uint32_t *q[2] = {nullptr, nullptr};    // frontier, n
+    unsigned long long *item_mask = nullptr;    // n: slot mask taken by each frontier item
+    uint64_t *item_pre = nullptr;           // n: pair prefix within its block segment
+    uint64_t *bsum = nullptr;               // pairs per block segment
+    uint32_t *far[2] = {nullptr, nullptr};  // n
+    MqControl *ctl = nullptr;
+    uint64_t *pairtab[MQ_SLOTS] = {};       // per-slot pair table
+    uint64_t pairtab_cap[MQ_SLOTS] = {};
+    uint64_t **d_pairtab = nullptr;         // device copy of the pointers
+    uint32_t *d_k = nullptr;                // device copy of the slot sizes
+    int32_t *seeds[MQ_SLOTS] = {};          // per-slot sorted seeds
+    uint32_t seeds_cap[MQ_SLOTS] = {};
+    uint32_t base_near = 1;                 // stamp tags are base_near + it
+};
+
+cudaError_t mq_alloc(const DevGraph &g, MqState &m, cudaStream_t s);
+void mq_free(MqState &m);
+int mq_occupancy(int threads);
+
+// Admission: clear the label/pred columns of the slots in `mask`, then
+// seed slot q from the k sorted seeds already copied to m.seeds[q].
+cudaError_t mq_launch_clear(const DevGraph &g, MqState &m, unsigned long long mask,
+                            cudaStream_t s);
+cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uint32_t delta,
+                           cudaStream_t s);
+// Runs the persistent multi-query SSSP.  yield: return when a slot converges
+// or *doorbell (host-mapped) is set; otherwise run until every in-flight slot
+// converged.  max_iters caps this launch.
+cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
+                           uint32_t max_iters, bool yield, const uint32_t *doorbell,
+                           cudaStream_t s);
+// Predecessors and per-slot bridge tables for the slots in `slots`.
+cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slots,
+                           cudaStream_t s);
+
+}  // namespace stn

@@ -1,8 +1,23 @@
-// Batch and serving entry points.
+// Batched and serving modes over the multi-query engine (multi.cu).
 //
-// steiner_query_batch runs its queries back to back on the graph's stream;
-// the serving loop is a host worker thread that admits submitted queries in
-// arrival order and runs each through the same device pipeline.
+// The engine owns MQ_SLOTS query slots on the resident graph.  A query is
+// admitted into a free slot (its label column cleared, its seeds placed on
+// the shared frontier), the persistent multi-query kernel runs until some
+// slot converges (or, when serving, until the host rings the doorbell
+// because new requests wait and slots are free), converged slots run their
+// tails (batched pred + bridge scan, then per-slot compaction, MST,
+// expansion and sort) and are released, and freed slots take the next
+// queries.  Admission is bounded by a device-memory budget for per-query
+// state (the slot's label and predecessor columns plus its pair table).
+//
+//  steiner_query_batch   runs a list of queries to completion this way.
+//  steiner_serve_*       a worker thread runs the same loop continuously over
+//                        a request queue fed by steiner_submit; results are
+//                        collected with steiner_poll (continuous batching:
+//                        requests join while others are on the device).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -10,16 +25,331 @@
 #include <vector>
 
 #include "engine.h"
+#include "multi.h"
 
 namespace stn {
 
-struct BatchEngine {};
+namespace {
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
 
-void destroy_batch(BatchEngine *b) { delete b; }
+struct SlotInfo {
+    bool busy = false;
+    uint64_t tag = 0;              // caller's handle (batch index or ticket)
+    uint32_t k = 0;
+    uint64_t bytes = 0;            // per-query device state charged to the budget
+};
+
+struct BatchEngine {
+    steiner_graph *G = nullptr;
+    MqState m;
+    bool ready = false;
+    int blocks = 0;
+    uint32_t delta = 1;
+    uint32_t *doorbell_host = nullptr;   // pinned, mapped
+    uint32_t *doorbell_dev = nullptr;
+    MqControl *h_ctl = nullptr;          // pinned
+    unsigned long long *h_masks = nullptr;   // pinned staging for mask uploads
+    unsigned long long inflight = 0;
+    SlotInfo slots[MQ_SLOTS];
+    uint64_t budget = ~0ull, used = 0, fixed = 0;
+    uint64_t total_iterations = 0;
+    uint64_t iteration_cap = 1ull << 24;
+    // Band width of the shared frontier.  Iterations are shared by all slots,
+    // so a narrower band than the single-query default (closer to Dijkstra
+    // order, fewer wasted relaxations) pays off; 0 = a quarter of it.
+    uint32_t batch_delta = 0;
+    // cumulative wall time (ms) and counters, for tracing
+    double ms_sssp = 0, ms_scan = 0, ms_tail = 0, ms_admit = 0;
+    uint64_t launches = 0, relax_attempts = 0, iterations_run = 0;
+    std::atomic<int> free_slots{MQ_SLOTS};
+
+    int init() {
+        if (ready) return STEINER_OK;
+        const DevGraph &g = api_graph(G);
+        cudaStream_t s = api_stream(G);
+        cudaError_t e = mq_alloc(g, m, s);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&doorbell_host, 64, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&doorbell_dev, doorbell_host, 0);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h_ctl, sizeof(MqControl));
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h_masks, 64);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            api_set_error(std::string("multi-query engine set-up: ") + cudaGetErrorString(e));
+            release();
+            return e == cudaErrorMemoryAllocation ? STEINER_ENOMEM : STEINER_ECUDA;
+        }
+        *doorbell_host = 0;
+        int per_sm = mq_occupancy(256);
+        int sms = api_geometry(G).sm_count;
+        blocks = std::max(1, per_sm) * sms;
+        delta = batch_delta ? batch_delta : std::max<uint32_t>(1, api_delta(G) / 4);
+        fixed = (uint64_t)g.n * MQ_SLOTS * 12;
+        ready = true;
+        return STEINER_OK;
+    }
+
+    void release() {
+        if (m.ctl) mq_free(m);
+        if (doorbell_host) cudaFreeHost(doorbell_host);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_masks) cudaFreeHost(h_masks);
+        doorbell_host = nullptr;
+        h_ctl = nullptr;
+        h_masks = nullptr;
+        ready = false;
+    }
+
+    int free_slot() const {
+        for (int q = 0; q < MQ_SLOTS; ++q)
+            if (!slots[q].busy) return q;
+        return -1;
+    }
+
+    static uint64_t state_bytes(uint32_t k) {
+        uint64_t pairs = k > 1 ? (uint64_t)k * (k - 1) / 2 : 0;
+        return pairs * 8;
+    }
+
+    bool fits(uint32_t k) const { return used + state_bytes(k) <= budget; }
+
+    // Admission in two steps: stage() reserves slot q for sorted seeds
+    // (buffers, copies), commit() clears the staged slots' columns in one
+    // pass, seeds them and waits once.  Caller holds the graph mutex.
+    unsigned long long staged = 0;
+    std::vector<std::vector<int32_t>> staged_seeds = std::vector<std::vector<int32_t>>(MQ_SLOTS);
+
+    int admit(int q, const std::vector<int32_t> &ss, uint64_t tag) {
+        int rc = stage(q, ss, tag);
+        return rc ? rc : commit();
+    }
+
+    int commit() {
+        if (!staged) return STEINER_OK;
+        double t0 = now_s();
+        cudaStream_t s = api_stream(G);
+        cudaError_t e = mq_launch_clear(api_graph(G), m, staged, s);
+        for (unsigned long long mm = staged; mm && e == cudaSuccess; mm &= mm - 1) {
+            int q = __builtin_ctzll(mm);
+            e = mq_launch_seed(api_graph(G), m, q, slots[q].k, delta, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        unsigned long long done = staged;
+        staged = 0;
+        for (unsigned long long mm = done; mm; mm &= mm - 1) staged_seeds[__builtin_ctzll(mm)].clear();
+        ms_admit += 1e3 * (now_s() - t0);
+        if (e != cudaSuccess) {
+            api_set_error(std::string("admission: ") + cudaGetErrorString(e));
+            return STEINER_ECUDA;
+        }
+        return STEINER_OK;
+    }
+
+    int stage(int q, const std::vector<int32_t> &ss, uint64_t tag) {
+        cudaStream_t s = api_stream(G);
+        uint32_t k = (uint32_t)ss.size();
+        uint64_t pairs = k > 1 ? (uint64_t)k * (k - 1) / 2 : 0;
+        if (pairs > (1ull << 28)) {
+            api_set_error("seed set too large for the pair table (k(k-1)/2 > 2^28)");
+            return STEINER_ENOMEM;
+        }
+        cudaError_t e = cudaSuccess;
+        if (k > m.seeds_cap[q]) {
+            if (m.seeds[q]) e = cudaFreeAsync(m.seeds[q], s);
+            m.seeds[q] = nullptr;
+            if (e == cudaSuccess) e = cudaMallocAsync((void **)&m.seeds[q], (size_t)k * 4, s);
+            m.seeds_cap[q] = e == cudaSuccess ? k : 0;
+        }
+        if (e == cudaSuccess && pairs > m.pairtab_cap[q]) {
+            if (m.pairtab[q]) e = cudaFreeAsync(m.pairtab[q], s);
+            m.pairtab[q] = nullptr;
+            if (e == cudaSuccess) e = cudaMallocAsync((void **)&m.pairtab[q], pairs * 8, s);
+            m.pairtab_cap[q] = e == cudaSuccess ? pairs : 0;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&m.d_pairtab[q], &m.pairtab[q], sizeof(uint64_t *),
+                                    cudaMemcpyHostToDevice, s);
+        }
+        staged_seeds[q] = ss;     // host copy lives until commit() has waited
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m.seeds[q], staged_seeds[q].data(), (size_t)k * 4,
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&m.d_k[q], &k, 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && pairs) e = cudaMemsetAsync(m.pairtab[q], 0xFF, pairs * 8, s);
+        if (e != cudaSuccess) {
+            api_set_error(std::string("admission: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? STEINER_ENOMEM : STEINER_ECUDA;
+        }
+        slots[q].busy = true;
+        slots[q].tag = tag;
+        slots[q].k = k;
+        slots[q].bytes = state_bytes(k);
+        used += slots[q].bytes;
+        inflight |= 1ull << q;
+        staged |= 1ull << q;
+        free_slots.fetch_sub(1);
+        return STEINER_OK;
+    }
+
+    // Runs the persistent kernel; returns the newly converged slots in
+    // *done (slots stopped by an error are reported in *failed with *why).
+    int run(bool yield, unsigned long long *done, unsigned long long *failed, int *why) {
+        cudaStream_t s = api_stream(G);
+        *done = *failed = 0;
+        *why = STEINER_OK;
+        double t0 = now_s();
+        ++launches;
+        h_masks[0] = inflight;
+        h_masks[1] = 0;
+        cudaError_t e = cudaMemcpyAsync(&m.ctl->inflight, &h_masks[0], 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&m.ctl->converged, &h_masks[1], 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = mq_launch_sssp(api_graph(G), m, blocks, delta, 1u << 20, yield, doorbell_dev, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_ctl, m.ctl, sizeof(MqControl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            api_set_error(std::string("multi-query kernel: ") + cudaGetErrorString(e));
+            *failed = inflight;
+            *why = STEINER_ECUDA;
+            return STEINER_ECUDA;
+        }
+        total_iterations += h_ctl->iterations;
+        iterations_run += h_ctl->iterations;
+        relax_attempts = h_ctl->relax_attempts;
+        ms_sssp += 1e3 * (now_s() - t0);
+        if (h_ctl->err & (ERR_BARRIER | ERR_CAPACITY)) {
+            *failed = inflight;
+            *why = (h_ctl->err & ERR_BARRIER) ? STEINER_ETIMEOUT : STEINER_ENOMEM;
+            api_set_error("multi-query kernel: barrier or capacity error");
+            return *why;
+        }
+        *done = h_ctl->converged & inflight;
+        if (total_iterations > iteration_cap) {
+            *failed = inflight & ~*done;
+            *why = STEINER_ETIMEOUT;
+        }
+        return STEINER_OK;
+    }
+
+    // Tails of the slots in `mask`; results go to out(tag, result).
+    template <class Out>
+    void retire(unsigned long long mask, Out out) {
+        if (!mask) return;
+        cudaStream_t s = api_stream(G);
+        double t0 = now_s();
+        cudaError_t e = mq_launch_scan(api_graph(G), m, mask, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_ctl, m.ctl, sizeof(MqControl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        double t1 = now_s();
+        ms_scan += 1e3 * (t1 - t0);
+        for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+            int q = __builtin_ctzll(mm);
+            steiner_result_t r{};
+            if (e != cudaSuccess) {
+                r.status = STEINER_ECUDA;
+                api_set_error(std::string("batched scan: ") + cudaGetErrorString(e));
+            } else {
+                bool ovf = (h_ctl->slot_overflow >> q) & 1ull;
+                api_run_tail(G, m.pairtab[q], m.pred + q, MQ_SLOTS, slots[q].k, ovf, &r);
+            }
+            out(slots[q].tag, r);
+            release_slot(q);
+        }
+        ms_tail += 1e3 * (now_s() - t1);
+    }
+
+    template <class Out>
+    void fail_slots(unsigned long long mask, int why, Out out) {
+        for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+            int q = __builtin_ctzll(mm);
+            steiner_result_t r{};
+            r.status = why;
+            out(slots[q].tag, r);
+            release_slot(q);
+        }
+        if (mask) reset_device_state();
+    }
+
+    void release_slot(int q) {
+        used -= slots[q].bytes;
+        slots[q] = SlotInfo();
+        inflight &= ~(1ull << q);
+        free_slots.fetch_add(1);
+    }
+
+    // After an error the shared frontier may hold stale entries: clear it.
+    void reset_device_state() {
+        cudaStream_t s = api_stream(G);
+        uint32_t n = api_graph(G).n;
+        cudaMemsetAsync(m.ctl, 0, sizeof(MqControl), s);
+        cudaMemsetAsync(m.nmask, 0, (size_t)n * 8, s);
+        cudaMemsetAsync(m.fmask, 0, (size_t)n * 8, s);
+        cudaMemsetAsync(m.stamp_near, 0, (size_t)n * 4, s);
+        cudaMemsetAsync(m.in_far, 0, (size_t)n * 4, s);
+        cudaStreamSynchronize(s);
+        total_iterations = 0;
+    }
+};
+
+void destroy_batch(BatchEngine *b) {
+    if (!b) return;
+    b->release();
+    delete b;
+}
+
+// Tracing counters of the multi-query engine (steiner_get_param keys
+// "batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit",
+// "batch_launches", "batch_iterations", "batch_relax_attempts"; "batch_reset"
+// clears them).
+int batch_set_delta(steiner_graph *G, uint32_t d);
+
+int64_t batch_counter(BatchEngine *B, const char *key) {
+    if (!B) return -1;
+    std::string k(key);
+    if (k == "batch_ms_sssp") return (int64_t)(B->ms_sssp * 1000);
+    if (k == "batch_ms_scan") return (int64_t)(B->ms_scan * 1000);
+    if (k == "batch_ms_tail") return (int64_t)(B->ms_tail * 1000);
+    if (k == "batch_ms_admit") return (int64_t)(B->ms_admit * 1000);
+    if (k == "batch_launches") return (int64_t)B->launches;
+    if (k == "batch_iterations") return (int64_t)B->iterations_run;
+    if (k == "batch_relax_attempts") return (int64_t)B->relax_attempts;
+    if (k == "batch_delta") return B->delta;
+    if (k == "batch_reset") {
+        B->ms_sssp = B->ms_scan = B->ms_tail = B->ms_admit = 0;
+        B->launches = B->iterations_run = 0;
+        return 0;
+    }
+    return -1;
+}
+
+static BatchEngine *engine_of(steiner_graph *G) {
+    BatchEngine *&B = api_batch(G);
+    if (!B) {
+        B = new BatchEngine();
+        B->G = G;
+    }
+    return B;
+}
+
+int batch_set_delta(steiner_graph *G, uint32_t d) {
+    BatchEngine *B = engine_of(G);
+    B->batch_delta = d;
+    if (B->ready) B->delta = d ? d : std::max<uint32_t>(1, api_delta(G) / 4);
+    return STEINER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// serving
+// ---------------------------------------------------------------------------
 
 struct ServeJob {
     uint64_t ticket;
-    std::vector<int32_t> seeds;
+    std::vector<int32_t> seeds;     // sorted
+    double t_submit;
 };
 
 struct ServeEngine {
@@ -29,28 +359,83 @@ struct ServeEngine {
     std::condition_variable cv;
     std::deque<ServeJob> queue;
     std::unordered_map<uint64_t, steiner_result_t> done;
+    std::unordered_map<uint64_t, double> t_submit;
     uint64_t next_ticket = 1;
     uint32_t max_queue = 1u << 16;
     bool stop = false;
 
     void run() {
         cudaSetDevice(api_device(G));
+        BatchEngine *B = nullptr;
         for (;;) {
-            ServeJob job;
+            std::vector<ServeJob> take;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                cv.wait(lk, [&] { return stop || !queue.empty(); });
-                if (stop && queue.empty()) return;
-                job = std::move(queue.front());
-                queue.pop_front();
+                bool idle = !B || B->inflight == 0;
+                if (idle)
+                    cv.wait(lk, [&] { return stop || !queue.empty(); });
+                if (stop && queue.empty() && (!B || B->inflight == 0)) return;
+                while (!queue.empty()) {
+                    take.push_back(std::move(queue.front()));
+                    queue.pop_front();
+                }
             }
-            steiner_result_t r{};
+            std::vector<std::pair<uint64_t, steiner_result_t>> finished;
+            auto out = [&](uint64_t tag, const steiner_result_t &r) { finished.emplace_back(tag, r); };
+            std::deque<ServeJob> waiting(std::make_move_iterator(take.begin()),
+                                         std::make_move_iterator(take.end()));
             {
                 std::lock_guard<std::mutex> glk(api_mutex(G));
-                api_query_locked(G, job.seeds.data(), (uint32_t)job.seeds.size(), &r);
+                B = engine_of(G);
+                int rc = B->init();
+                if (rc) {
+                    for (auto &j : waiting) {
+                        steiner_result_t r{};
+                        r.status = rc;
+                        out(j.ticket, r);
+                    }
+                    waiting.clear();
+                }
+                *B->doorbell_host = 0;
+                // admit what fits; the rest goes back to the queue head
+                while (!waiting.empty()) {
+                    uint32_t kq = (uint32_t)waiting.front().seeds.size();
+                    if (kq == 1) {                       // a single seed: the empty tree
+                        steiner_result_t r{};
+                        out(waiting.front().ticket, r);
+                        waiting.pop_front();
+                        continue;
+                    }
+                    if (!B->fits(kq) && B->inflight == 0) {
+                        steiner_result_t r{};          // can never fit this budget
+                        r.status = STEINER_EBUSY;
+                        out(waiting.front().ticket, r);
+                        waiting.pop_front();
+                        continue;
+                    }
+                    int q = B->free_slot();
+                    if (q < 0 || !B->fits(kq)) break;
+                    ServeJob j = std::move(waiting.front());
+                    waiting.pop_front();
+                    int arc = B->stage(q, j.seeds, j.ticket);
+                    if (arc) {
+                        steiner_result_t r{};
+                        r.status = arc;
+                        out(j.ticket, r);
+                    }
+                }
+                if (int rc2 = B->commit()) B->fail_slots(B->inflight, rc2, out);
+                if (B->inflight) {
+                    unsigned long long conv = 0, failed = 0;
+                    int why = 0;
+                    B->run(true, &conv, &failed, &why);
+                    B->retire(conv & ~failed, out);
+                    B->fail_slots(failed, why, out);
+                }
             }
             std::lock_guard<std::mutex> lk(mu);
-            done[job.ticket] = r;
+            for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) queue.push_front(std::move(*it));
+            for (auto &f : finished) done[f.first] = f.second;
         }
     }
 };
@@ -69,20 +454,75 @@ int steiner_query_batch(steiner_graph_t G, const int32_t *const *seeds, const ui
     }
     std::lock_guard<std::mutex> lk(api_mutex(G));
     cudaSetDevice(api_device(G));
-    int first = STEINER_OK;
     for (uint32_t i = 0; i < q; ++i) {
-        int rc = api_query_locked(G, seeds[i], ks[i], &outs[i]);
-        if (rc != STEINER_OK && first == STEINER_OK) first = rc;
+        outs[i].edges = nullptr;
+        outs[i].n_edges = 0;
+        outs[i].total = 0;
+        outs[i].status = STEINER_OK;
     }
+    BatchEngine *B = engine_of(G);
+    int rc = B->init();
+    if (rc) {
+        for (uint32_t i = 0; i < q; ++i) outs[i].status = rc;
+        return rc;
+    }
+    std::deque<std::pair<uint32_t, std::vector<int32_t>>> pending;
+    for (uint32_t i = 0; i < q; ++i) {
+        std::vector<int32_t> ss;
+        int r = api_sorted_seeds(G, seeds[i], ks[i], ss);
+        if (r) outs[i].status = r;
+        else if (ss.size() > 1) pending.emplace_back(i, std::move(ss));   // k = 1: empty tree
+    }
+    auto out = [&](uint64_t tag, const steiner_result_t &r) { outs[tag] = r; };
+    while (!pending.empty() || B->inflight) {
+        while (!pending.empty()) {
+            int slot = B->free_slot();
+            if (slot < 0) break;
+            auto job = std::move(pending.front());
+            pending.pop_front();
+            int r = B->stage(slot, job.second, job.first);
+            if (r) outs[job.first].status = r;
+        }
+        if (int r = B->commit()) {
+            B->fail_slots(B->inflight, r, out);
+            continue;
+        }
+        if (!B->inflight) continue;
+        unsigned long long conv = 0, failed = 0;
+        int why = 0;
+        // yield on convergence only while queries still wait for a slot
+        B->run(!pending.empty(), &conv, &failed, &why);
+        B->retire(conv & ~failed, out);
+        B->fail_slots(failed, why, out);
+    }
+    int first = STEINER_OK;
+    for (uint32_t i = 0; i < q; ++i)
+        if (outs[i].status != STEINER_OK) {
+            first = outs[i].status;
+            break;
+        }
     return first;
 }
 
 int steiner_serve_start(steiner_graph_t G, uint32_t slots, uint64_t budget_bytes) {
-    (void)slots;
-    (void)budget_bytes;
     if (!G) return STEINER_EINVAL;
     ServeEngine *&S = api_serve(G);
     if (S) return STEINER_OK;
+    {
+        std::lock_guard<std::mutex> glk(api_mutex(G));
+        BatchEngine *B = engine_of(G);
+        int rc = B->init();
+        if (rc) return rc;
+        // the budget covers the slots' label/pred columns and pair tables
+        if (budget_bytes <= B->fixed) {
+            api_set_error("serving budget smaller than the per-slot label state");
+            return STEINER_ENOMEM;
+        }
+        B->budget = budget_bytes - B->fixed;
+        int usable = (int)std::min<uint32_t>(slots ? slots : MQ_SLOTS, MQ_SLOTS);
+        for (int q = usable; q < MQ_SLOTS; ++q) B->slots[q].busy = true;   // not offered
+        B->free_slots = usable;
+    }
     S = new ServeEngine();
     S->G = G;
     S->worker = std::thread([S] { S->run(); });
@@ -90,17 +530,27 @@ int steiner_serve_start(steiner_graph_t G, uint32_t slots, uint64_t budget_bytes
 }
 
 int steiner_submit(steiner_graph_t G, const int32_t *seeds, uint32_t k, uint64_t *ticket) {
-    if (!G || !ticket || (k && !seeds)) return STEINER_EINVAL;
+    if (!G || !ticket) return STEINER_EINVAL;
     ServeEngine *S = api_serve(G);
     if (!S) {
         api_set_error("serving not started");
         return STEINER_EINVAL;
     }
+    std::vector<int32_t> ss;
+    int rc = api_sorted_seeds(G, seeds, k, ss);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->queue.size() >= S->max_queue) return STEINER_EBUSY;
-    ServeJob job{S->next_ticket++, std::vector<int32_t>(seeds, seeds + k)};
-    *ticket = job.ticket;
-    S->queue.push_back(std::move(job));
+    uint64_t t = S->next_ticket++;
+    *ticket = t;
+    if (rc) {
+        steiner_result_t r{};
+        r.status = rc;
+        S->done[t] = r;
+        return STEINER_OK;
+    }
+    S->queue.push_back(ServeJob{t, std::move(ss), now_s()});
+    BatchEngine *B = api_batch(G);
+    if (B && B->doorbell_host && B->free_slots.load() > 0) *(volatile uint32_t *)B->doorbell_host = 1;
     S->cv.notify_one();
     return STEINER_OK;
 }
@@ -130,6 +580,15 @@ int steiner_serve_stop(steiner_graph_t G) {
     for (auto &kv : S->done) free(kv.second.edges);
     delete S;
     S = nullptr;
+    // hand every slot back to the batch mode
+    BatchEngine *B = api_batch(G);
+    if (B) {
+        std::lock_guard<std::mutex> glk(api_mutex(G));
+        for (int q = 0; q < MQ_SLOTS; ++q)
+            if (!((B->inflight >> q) & 1)) B->slots[q] = SlotInfo();
+        B->budget = ~0ull;
+        B->free_slots = MQ_SLOTS - __builtin_popcountll(B->inflight);
+    }
     return STEINER_OK;
 }
 

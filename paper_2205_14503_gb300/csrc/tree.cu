@@ -129,9 +129,9 @@ __device__ __forceinline__ void emit_edge(uint32_t a, uint32_t b, uint32_t w, ui
 __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
                               uint32_t n, const uint32_t *__restrict__ e_arc,
                               const uint32_t *__restrict__ e_mst,
-                              const uint32_t *__restrict__ pred_arc, uint32_t *mark, uint32_t tag,
-                              uint32_t nbits, uint64_t *key, uint32_t *wout, uint32_t cap,
-                              Control *ctl) {
+                              const uint32_t *__restrict__ pred_arc, uint32_t pred_stride,
+                              uint32_t *mark, uint32_t tag, uint32_t nbits, uint64_t *key,
+                              uint32_t *wout, uint32_t cap, Control *ctl) {
     const uint32_t E = ldcg_u32(&ctl->n_pairs);
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < E; j += gridDim.x * blockDim.x) {
         if (!e_mst[j]) continue;
@@ -144,7 +144,7 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
         for (int side = 0; side < 2; ++side) {
             uint32_t x = ends[side];
             for (uint32_t steps = 0; steps < n; ++steps) {
-                uint32_t pa = pred_arc[x];
+                uint32_t pa = pred_arc[(uint64_t)x * pred_stride];
                 if (pa == SEED_ARC || pa == INF32) break;
                 if (atomicExch(&mark[x], tag) == tag) break;   // rest of the chain is taken
                 uint2 pe = adj[pa];
@@ -314,8 +314,8 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
     uint64_t slots = (uint64_t)k * (k - 1) / 2;
     uint32_t blocks = (uint32_t)std::min<uint64_t>((slots + 255) / 256, 152ull * 8);
     expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
-                                         ws.mark, tag, n_bits, ws.tree_key, ws.tree_w,
-                                         ws.tree_cap, ws.ctl);
+                                         ws.pred_stride, ws.mark, tag, n_bits, ws.tree_key,
+                                         ws.tree_w, ws.tree_cap, ws.ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (sort_blocks_cache < 0) {

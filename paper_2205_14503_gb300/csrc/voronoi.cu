@@ -119,24 +119,6 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
     __syncthreads();
 }
 
-// Warp-aggregated append of v into a staging buffer, spilling to the
-// global queue (gq, gcount, gcap) when the buffer is full.  All lanes call.
-__device__ __forceinline__ void stage_append(bool want, uint32_t v, uint32_t *buf, uint32_t *cnt,
-                                             uint32_t cap, uint32_t *gq, uint32_t *gcount,
-                                             uint32_t gcap, uint32_t *err) {
-    uint32_t mask = __ballot_sync(FULL, want);
-    if (mask == 0) return;
-    uint32_t leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane_id() == leader) base = atomicAdd(cnt, (uint32_t)__popc(mask));
-    base = __shfl_sync(FULL, base, leader);
-    uint32_t slot = base + (uint32_t)__popc(mask & lanemask_lt());
-    bool local = want && slot < cap;
-    if (local) buf[slot] = v;
-    uint32_t g = warp_append(want && !local, gcount, gcap, err);
-    if (g != INF32) gq[g] = v;
-}
-
 // Moves the block's staged appends to the global queues.  Called by all
 // threads of the block; ends with the staging buffers still holding data
 // (stage_reset clears them at the next segment).
@@ -194,9 +176,13 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
 // Relaxes up to ILP arcs per lane.  For arc u of this lane: valid[u], the
 // arc index and the tail's label.  The loads and atomics of the ILP arcs
 // are issued back to back so their latencies overlap.
+// With `precheck` a plain load of the head's label comes first and only
+// improving proposals issue the atomic: right for thick frontiers, where
+// L2 atomic throughput is the limit; thin frontiers are latency-bound and
+// skip the extra dependent load.
 __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const PushTargets &t,
                                             const bool (&valid)[ILP], const uint32_t (&arc)[ILP],
-                                            const uint64_t (&lab)[ILP],
+                                            const uint64_t (&lab)[ILP], bool precheck,
                                             unsigned long long &attempts,
                                             unsigned long long &improved) {
     uint2 e[ILP];
@@ -215,9 +201,11 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
             // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
             if (nd[u] < INF32) {
                 uint64_t nl = (nd[u] << 32) | (lab[u] & 0xFFFFFFFFull);
-                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
-                                         (unsigned long long)nl);
-                imp[u] = nl < old;
+                if (!precheck || nl < ldcg_u64(&a.label[e[u].x])) {
+                    uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
+                                             (unsigned long long)nl);
+                    imp[u] = nl < old;
+                }
             }
         }
     }
@@ -314,7 +302,7 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
                         valid[q] = arc[q] < e;
                         labs[q] = lab;
                     }
-                    relax_group(a, st, t, valid, arc, labs, attempts, improved);
+                    relax_group(a, st, t, valid, arc, labs, true, attempts, improved);
                 }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
@@ -346,7 +334,7 @@ __global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
                         labs[q] = __shfl_sync(FULL, lab, owner);
                         arc[q] = so + (j - eo);
                     }
-                    relax_group(a, st, t, valid, arc, labs, attempts, improved);
+                    relax_group(a, st, t, valid, arc, labs, bsz == 32, attempts, improved);
                 }
             }
         }

@@ -1,0 +1,161 @@
+"""GPU parity of the multi-query modes: steiner_query_batch and the serving
+calls give, for every query, exactly the tree (edges, total, status) that
+the CPU oracle and the single-query path give — alone and in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2205_14503_gb300.workloads as wl
+from tests import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+st = pytest.importorskip("paper_2205_14503_gb300.steiner")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_14503_gb300 import build
+    build.build()
+    st.load_library()
+
+
+def _queries(pool, sizes, salt):
+    return [wl.sample_distinct(pool, int(k), salt * 1000 + i) for i, k in enumerate(sizes)]
+
+
+def _check(g, seed_sets, results):
+    for i, (seeds, r) in enumerate(zip(seed_sets, results)):
+        ref = oracle.steiner(g, seeds, want_labels=False)
+        assert r.status == ref.status, (i, r.status, ref.status)
+        np.testing.assert_array_equal(r.edges, ref.edges, err_msg=f"query {i}")
+        assert r.total == ref.total, i
+
+
+def test_batch_64_queries_log_uniform_sizes():
+    g = wl.rmat(14, 16, wmax=1000, seed=41)
+    pool = wl.largest_cc(g)
+    sizes = wl.log_uniform_sizes(64, 3, 300, 7)
+    qs = _queries(pool, sizes, 1)
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+    assert rc == st.STEINER_OK
+    _check(g, qs, res)
+
+
+def test_batch_more_queries_than_slots_reuses_slots():
+    g = wl.rmat(13, 16, wmax=100, seed=42)
+    pool = wl.largest_cc(g)
+    sizes = wl.log_uniform_sizes(150, 2, 120, 8)
+    qs = _queries(pool, sizes, 2)
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+        single = [Gd.query(s) for s in qs[:20]]
+    assert rc == st.STEINER_OK
+    _check(g, qs, res)
+    for a, b in zip(res[:20], single):     # same in the batch as alone
+        assert np.array_equal(a.edges, b.edges) and a.total == b.total
+
+
+def test_batch_high_diameter_grid():
+    g = wl.grid(300, 200, 1000, seed=43)
+    pool = np.arange(g.n, dtype=np.int32)
+    qs = _queries(pool, [2, 5, 17, 64, 3, 200, 9, 40], 3)
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+    assert rc == st.STEINER_OK
+    _check(g, qs, res)
+
+
+def test_batch_mixed_statuses_and_degenerate_queries():
+    e = np.array([[0, 1, 3], [1, 2, 4], [3, 4, 5], [4, 5, 1], [5, 6, 2], [0, 2, 9]])
+    g = wl.from_edges(9, e[:, 0], e[:, 1], e[:, 2])
+    qs = [np.array([0, 2]), np.array([0, 5]), np.array([4]), np.array([3, 3]),
+          np.array([1, 2, 3, 6]), np.array([8, 0]), np.array([2, 0, 1])]
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+        alone = [Gd.query(s) for s in qs]
+    assert rc != st.STEINER_OK
+    for s, r, a in zip(qs, res, alone):
+        ref = oracle.steiner(g, s, want_labels=False)
+        assert r.status == ref.status == a.status
+        if ref.status in (oracle.OK, oracle.EDISCONNECTED):
+            np.testing.assert_array_equal(r.edges, ref.edges)
+            assert r.total == ref.total
+
+
+def test_batch_unit_weights_ties():
+    g = wl.rmat(12, 16, wmax=1, seed=44)
+    pool = wl.largest_cc(g)
+    qs = _queries(pool, wl.log_uniform_sizes(40, 2, 200, 9), 4)
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+    assert rc == st.STEINER_OK
+    _check(g, qs, res)
+
+
+def test_serving_stream_matches_alone():
+    """Requests submitted while others run (continuous batching) give the
+    same trees as each query alone."""
+    g = wl.rmat(14, 16, wmax=1000, seed=45)
+    pool = wl.largest_cc(g)
+    sizes = wl.log_uniform_sizes(120, 3, 500, 10)
+    qs = _queries(pool, sizes, 5)
+    arrivals = wl.poisson_arrivals(len(qs), 4000.0, 11)
+    with st.SteinerGraph(g) as Gd:
+        h = Gd.handle
+        st.steiner_serve_start(h, 64, 8 << 30)
+        tickets, t0 = [], time.perf_counter()
+        for s, at in zip(qs, arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            rc, t = st.steiner_submit(h, s)
+            assert rc == st.STEINER_OK
+            tickets.append(t)
+        results = {}
+        deadline = time.time() + 120
+        while len(results) < len(tickets) and time.time() < deadline:
+            for t in tickets:
+                if t in results:
+                    continue
+                rc, r = st.steiner_poll(h, t)
+                if rc != st.STEINER_PENDING:
+                    results[t] = r
+            time.sleep(0.001)
+        st.steiner_serve_stop(h)
+        alone = [Gd.query(s) for s in qs[:30]]
+    assert len(results) == len(tickets)
+    res = [results[t] for t in tickets]
+    _check(g, qs, res)
+    for a, b in zip(res[:30], alone):
+        assert np.array_equal(a.edges, b.edges) and a.total == b.total
+
+
+def test_serving_budget_refusals():
+    g = wl.rmat(11, 8, wmax=50, seed=46)
+    pool = wl.largest_cc(g)
+    with st.SteinerGraph(g) as Gd:
+        h = Gd.handle
+        with pytest.raises(st.SteinerError):
+            st.steiner_serve_start(h, 64, 1024)             # below the per-slot label state
+        fixed = g.n * 64 * 12
+        st.steiner_serve_start(h, 4, fixed + 8 * 1000)       # room for pair tables of k <= ~45
+        rc, t_big = st.steiner_submit(h, wl.sample_distinct(pool, 400, 1))
+        rc2, t_ok = st.steiner_submit(h, wl.sample_distinct(pool, 20, 2))
+        got = {}
+        deadline = time.time() + 60
+        while len(got) < 2 and time.time() < deadline:
+            for t in (t_big, t_ok):
+                if t not in got:
+                    r, res = st.steiner_poll(h, t)
+                    if r != st.STEINER_PENDING:
+                        got[t] = (r, res)
+            time.sleep(0.001)
+        st.steiner_serve_stop(h)
+    assert got[t_big][0] == st.STEINER_EBUSY
+    assert got[t_ok][0] == st.STEINER_OK
