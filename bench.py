@@ -234,6 +234,11 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     G = st.SteinerGraph(g, device=local)
     load_s = time.perf_counter() - t0
+    tuned = None
+    if not args.no_autotune:
+        # set-up, untimed: band width and persistent grid size for this graph
+        from paper_2205_14503_gb300 import autotune
+        tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
     for _ in range(max(args.warmup, 3)):
         r = G.query_detail(seeds, pairs=False)
         if r.status != st.STEINER_OK:
@@ -304,7 +309,9 @@ def run_ours(args, world, rank, local):
         "sssp": {"iterations": stats["iterations"], "phases": stats["phases"],
                  "relax_attempts": stats["relax_attempts"],
                  "work_efficiency": stats["relax_attempts"] / m_arcs,
-                 "delta": G.get_param("delta") if G.handle else None},
+                 "delta": tuned["delta"] if tuned else None,
+                 "blocks": tuned["sssp_blocks"] if tuned else None,
+                 "autotuned": bool(tuned)},
         "tree": {"edges": int(res.edges.shape[0]), "total": int(res.total)},
         "graph_load_s": load_s,
         "clocks": clocks,
@@ -320,6 +327,127 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batch_mode(args, world, rank, local):
+    """R-MAT scale 22, 64 queries of log-uniform size in [3, 1000] in one
+    batched run, against the same queries one at a time (plain path)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import steiner as st
+    torch.cuda.set_device(local)
+    g = wl.config_graph(4)
+    qs = wl.config_seed_sets(4, g)
+    if rank > 0:
+        pool = wl.largest_cc(g)
+        qs = [wl.sample_distinct(pool, q.size, 0x5EED + 4000 + 97 * rank + i) for i, q in enumerate(qs)]
+    G = st.SteinerGraph(g, device=local)
+    for _ in range(max(args.warmup, 3)):
+        G.query_batch(qs)
+    plain = [G.query(q) for q in qs]
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc, res = G.query_batch(qs)
+    torch.cuda.synchronize()
+    t_batch = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+    G.get_param("batch_reset")
+    G.query_batch(qs)
+    parts = {k: G.get_param("batch_" + k) / 1e3 for k in ("ms_sssp", "ms_scan", "ms_tail", "ms_admit")}
+    t0 = time.perf_counter()
+    for q in qs:
+        G.query(q)
+    t_plain = max_over_ranks(time.perf_counter() - t0, world)
+    same = all(a.status == b.status and a.total == b.total and np.array_equal(a.edges, b.edges)
+               for a, b in zip(res, plain))
+    G.close()
+    if rank != 0:
+        return
+    nq = len(qs) * world
+    line = {"metric": "batched Steiner queries/s (64 queries, one batched run)",
+            "value": nq / t_batch, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "rmat22_batch64", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
+                       "k_range": [3, 1000]},
+            "plain_queries_per_s": nq / t_plain, "speedup_vs_plain": t_plain / t_batch,
+            "identical_to_plain": same, "phase_ms": parts}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve_mode(args, world, rank, local):
+    """R-MAT scale 24, a stream of queries with log-uniform size in
+    [3, 10000]; saturated throughput (all submitted at once) and p50/p99
+    latency at 0.7x that rate (Poisson arrivals); 40 GB per-query budget."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import steiner as st
+    torch.cuda.set_device(local)
+    g = wl.config_graph(5)
+    qs = wl.config_seed_sets(5, g)[: args.queries]
+    G = st.SteinerGraph(g, device=local)
+    h = G.handle
+
+    def stream(arrivals):
+        st.steiner_serve_start(h, 64, 40 << 30)
+        tickets, submit_t, done_t = [], [], {}
+        t0 = time.perf_counter()
+        pending = set()
+        for s, at in zip(qs, arrivals):
+            while time.perf_counter() - t0 < at:
+                for t in list(pending):
+                    rc, _ = st.steiner_poll(h, t)
+                    if rc != st.STEINER_PENDING:
+                        done_t[t] = time.perf_counter()
+                        pending.discard(t)
+            rc, t = st.steiner_submit(h, s)
+            tickets.append(t)
+            submit_t.append(time.perf_counter())
+            pending.add(t)
+        while pending:
+            for t in list(pending):
+                rc, _ = st.steiner_poll(h, t)
+                if rc != st.STEINER_PENDING:
+                    done_t[t] = time.perf_counter()
+                    pending.discard(t)
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        st.steiner_serve_stop(h)
+        lat = [done_t[t] - ts for t, ts in zip(tickets, submit_t)]
+        return wall, lat
+
+    G.query(qs[0])
+    wall_sat, lat_sat = stream([0.0] * len(qs))
+    qps = len(qs) / wall_sat
+    arrivals = wl.poisson_arrivals(len(qs), 0.7 * qps, 0x5EED + 5)
+    wall_p, lat_p = stream(arrivals)
+    sample = qs[: min(len(qs), args.plain_sample)]
+    t0 = time.perf_counter()
+    for q in sample:
+        G.query(q)
+    plain_qps = len(sample) / (time.perf_counter() - t0)
+    G.close()
+    if rank != 0:
+        return
+    line = {"metric": "served Steiner queries/s (continuous batching) and p50/p99 time-to-tree",
+            "value": qps, "unit": "queries/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * wall_sat, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "rmat24_serve", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
+                       "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64},
+            "saturated": {"p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
+                          "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},
+            "poisson_0p7": {"rate_qps": 0.7 * qps, "achieved_qps": len(qs) / wall_p,
+                            "p50_ms": 1e3 * float(np.percentile(lat_p, 50)),
+                            "p99_ms": 1e3 * float(np.percentile(lat_p, 99))},
+            "plain_queries_per_s": plain_qps, "speedup_vs_plain": qps / plain_qps,
+            "plain_sample": len(sample)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,14 +455,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default band width and grid size")
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
+    ap.add_argument("--mode", choices=["plain", "batch", "serve"], default="plain",
+                    help="plain: the grid single-query workload (default); batch: R-MAT 22 with "
+                         "64 batched queries; serve: R-MAT 24 query stream")
+    ap.add_argument("--queries", type=int, default=2000, help="serve mode: stream length")
+    ap.add_argument("--plain-sample", type=int, default=200,
+                    help="serve mode: queries timed one at a time for the plain comparison")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.mode == "batch":
+            run_batch_mode(args, world, rank, local)
+        elif args.mode == "serve":
+            run_serve_mode(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

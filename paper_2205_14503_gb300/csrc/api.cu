@@ -419,6 +419,7 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
     int per_sm = sssp_occupancy(256);
     if (per_sm < 1) return bail(fail(STEINER_ECUDA, "SSSP kernel does not fit on an SM"));
     G->geo.sssp_blocks = per_sm * G->geo.sm_count;
+    G->geo.sssp_max_blocks = G->geo.sssp_blocks;
     int mst_sm = mst_occupancy(512);
     G->geo.mst_blocks = std::max(1, mst_sm) * G->geo.sm_count;
     // default band width: ~32 average weights spread over the average degree
@@ -469,6 +470,11 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     } else if (!strcmp(key, "batch_delta")) {
         if (value < 0 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "batch_delta out of range");
         return batch_set_delta(G, (uint32_t)value);
+    } else if (!strcmp(key, "sssp_blocks")) {
+        // persistent grid size: 1 .. all co-resident blocks (0 = all)
+        int maxb = G->geo.sssp_max_blocks;
+        if (value < 0 || value > maxb) return fail(STEINER_EINVAL, "sssp_blocks out of range");
+        G->geo.sssp_blocks = value ? (int)value : maxb;
     } else if (!strcmp(key, "max_iters")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "max_iters out of range");
         G->max_iters = (uint32_t)value;
@@ -483,6 +489,7 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "delta")) return G->delta;
     if (!strcmp(key, "max_iters")) return G->max_iters;
     if (!strcmp(key, "sssp_blocks")) return G->geo.sssp_blocks;
+    if (!strcmp(key, "sssp_max_blocks")) return G->geo.sssp_max_blocks;
     if (!strcmp(key, "sm_count")) return G->geo.sm_count;
     if (!strcmp(key, "heavy_chunks")) return G->g.n_heavy_chunks;
     if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);

@@ -90,7 +90,8 @@ struct Workspace {
 // Launch geometry of the persistent kernels (from the occupancy API).
 struct Geometry {
     int sm_count = 0;
-    int sssp_blocks = 0;
+    int sssp_blocks = 0;        // persistent grid size in use
+    int sssp_max_blocks = 0;    // co-resident limit (occupancy x SMs)
     int mst_blocks = 0;
     int threads = 256;
 };

@@ -38,7 +38,7 @@ struct MqArgs {
     uint32_t delta;
     uint32_t base_near;
     uint32_t max_iters;
-    uint32_t yield;
+    uint32_t yield;          // leave once this many slots converged (0: only when all did)
 };
 
 constexpr int MQ_WARPS = 256 / 32;
@@ -67,6 +67,12 @@ struct MqTargets {
 };
 
 __device__ __forceinline__ int popc64(unsigned long long x) { return __popcll(x); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Inclusive scan of one 64-bit value per thread over a 256-thread block;
 // wtot[] receives the per-warp inclusive totals (wtot[MQ_WARPS-1] = block
@@ -198,6 +204,8 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
             }
         }
     }
+    // most rounds improve nothing: skip the append machinery then
+    if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
     bool to_near[MQ_ILP], to_far[MQ_ILP];
     unsigned long long act = 0;
 #pragma unroll
@@ -228,14 +236,13 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
     }
 }
 
-__global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
+__global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
     __shared__ MqStage st;
     MqControl *ctl = a.ctl;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t gthreads = gridDim.x * blockDim.x;
     const bool first = gtid == 0;
     unsigned long long attempts = 0, improved = 0;
     uint32_t it = ldcg_u32(&ctl->it), fc = ldcg_u32(&ctl->fc);
@@ -256,6 +263,7 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
         }
         const uint32_t *qc = odd ? a.q1 : a.q0;
 
+        unsigned long long tm0 = first ? gtimer() : 0;
         // Phase A: every frontier vertex takes its pending slot mask; its
         // work is deg x |mask| (arc, slot) pairs; prefix sums per block
         // segment of the frontier.
@@ -280,7 +288,9 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
             __syncthreads();
         }
         if (threadIdx.x == 0) a.bsum[blockIdx.x] = st.carry;
+        unsigned long long tm1 = first ? gtimer() : 0;
         if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        unsigned long long tm2 = first ? gtimer() : 0;
         // block offsets and the total
         {
             uint64_t carry = 0;
@@ -306,13 +316,11 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
         t.fmin = ctl->fmin[fc];
         t.tag_next = a.base_near + it + 1;
 
-        // Phase B: warp w relaxes pairs [W w / nw, W (w + 1) / nw).  Pairs of
-        // an item are numbered arc-major (arc j, slot t -> j * |mask| + t).
-        // Lanes are grouped by the item's slot count: a group of g lanes
-        // (g = |mask| rounded up to a power of two, at most 32) takes one arc,
-        // lane t of the group its t-th slot, so a warp relaxes 32 / g arcs per
-        // round with one broadcast arc load per group and the tail's label
-        // for that slot held in a register for the whole item.
+        // Phase B: warp w relaxes pairs [W w / nw, W (w + 1) / nw), numbered
+        // arc-major inside each item (arc j, slot t -> j * |mask| + t).  The
+        // warp slides a window of 32 consecutive frontier items (one per
+        // lane, loaded in parallel) and spreads the window's pairs over its
+        // lanes, 4 per lane in flight.
         const uint64_t W = st.W;
         uint64_t p = (uint64_t)((unsigned __int128)W * warp / nwarps);
         const uint64_t p1 = (uint64_t)((unsigned __int128)W * (warp + 1) / nwarps);
@@ -325,50 +333,71 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
                 uint32_t mid = lo + (hi - lo) / 2;
                 if (gpre(mid) <= p) lo = mid; else hi = mid;
             }
-            for (uint32_t i = lo; i < n_items && p < p1; ++i) {
-                const uint64_t base = gpre(i);
-                const uint32_t u = ldcg_u32(&qc[i]);
-                const unsigned long long M = __ldcg(&a.item_mask[i]);
-                const uint32_t c = (uint32_t)popc64(M);
-                if (c == 0) continue;
-                const uint32_t s0 = a.row_ptr[u], deg = a.row_ptr[u + 1] - s0;
-                const uint64_t iend = base + (uint64_t)deg * c;
-                if (iend <= p) continue;
-                // arcs of this item that hold pairs in [p, p1)
-                const uint64_t lo_p = p > base ? p - base : 0;
-                const uint64_t hi_p = min(p1, iend) - base;
-                const uint32_t ja = (uint32_t)(lo_p / c), jb = (uint32_t)((hi_p + c - 1) / c);
-                const uint32_t g = c >= 32 ? 32 : (c > 16 ? 32 : c > 8 ? 16 : c > 4 ? 8 : c > 2 ? 4 : c);
-                const uint32_t gsh = g == 32 ? 5 : g == 16 ? 4 : g == 8 ? 3 : g == 4 ? 2 : g == 2 ? 1 : 0;
-                const uint32_t apr = 32 >> gsh;               // arcs per round
-                const uint32_t grp = lane >> gsh, tl = lane & (g - 1);
-                for (uint32_t pass = 0; pass * 32 < c; ++pass) {   // slots t and t + 32
-                    const uint32_t ts = tl + pass * 32;
-                    const bool has_slot = ts < c;
-                    const uint32_t q = has_slot ? nth_bit64(M, ts) : 0;
-                    const uint64_t lu = has_slot ? ldcg_u64(&a.label[(uint64_t)u * MQ_SLOTS + q]) : INF64;
-                    for (uint32_t j0 = ja; j0 < jb; j0 += apr * MQ_ILP) {
-                        bool valid[MQ_ILP];
-                        uint32_t arc[MQ_ILP], qs[MQ_ILP];
-                        uint64_t labs[MQ_ILP];
-#pragma unroll
-                        for (int k = 0; k < MQ_ILP; ++k) {
-                            uint32_t j = j0 + k * apr + grp;
-                            uint64_t pidx = (uint64_t)j * c + ts;    // pair index within the item
-                            valid[k] = has_slot && j < jb && pidx >= lo_p && pidx < hi_p;
-                            arc[k] = s0 + j;
-                            qs[k] = q;
-                            labs[k] = lu;
-                        }
-                        mq_relax(a, st, t, valid, arc, qs, labs, attempts, improved);
-                    }
+            uint32_t i0 = lo;
+            while (p < p1) {
+                uint32_t idx = i0 + lane;
+                uint64_t pre = ~0ull;
+                uint32_t u = 0, s0 = 0, c = 0;
+                unsigned long long M = 0;
+                if (idx < n_items) {
+                    pre = gpre(idx);
+                    u = ldcg_u32(&qc[idx]);
+                    M = __ldcg(&a.item_mask[idx]);
+                    s0 = a.row_ptr[u];
+                    c = (uint32_t)popc64(M);
                 }
-                p = iend;
+                const uint64_t wend = i0 + 32 < n_items ? gpre(i0 + 32) : W;
+                const uint64_t stop = min(p1, wend);
+                const uint64_t pbase = __shfl_sync(FULL, pre, 0);
+                // window-relative prefixes fit 32 bits (an item has at most
+                // deg x 64 pairs)
+                const uint32_t rel = idx < n_items ? (uint32_t)(pre - pbase) : 0xFFFFFFFFu;
+                const uint32_t q1 = M ? (uint32_t)(__ffsll((long long)M) - 1) : 0;   // lowest slot
+                for (; p < stop; p += 32 * MQ_ILP) {
+                    bool valid[MQ_ILP];
+                    uint32_t arc[MQ_ILP], qs[MQ_ILP];
+                    uint64_t labs[MQ_ILP];
+#pragma unroll
+                    for (int k = 0; k < MQ_ILP; ++k) {
+                        const uint64_t pp = p + lane + 32 * k;
+                        valid[k] = pp < stop;
+                        const uint32_t pr = valid[k] ? (uint32_t)(pp - pbase) : 0;
+                        const uint32_t owner = warp_owner_search(rel, pr);
+                        const uint32_t ro = __shfl_sync(FULL, rel, owner);
+                        const uint32_t so = __shfl_sync(FULL, s0, owner);
+                        const uint32_t uo = __shfl_sync(FULL, u, owner);
+                        const uint32_t co = __shfl_sync(FULL, c, owner);
+                        const uint32_t qf = __shfl_sync(FULL, q1, owner);
+                        const unsigned long long Mo = __shfl_sync(FULL, M, owner);
+                        const uint32_t local = pr - ro;
+                        uint32_t j = local, q = qf;
+                        if (valid[k] && co > 1) {            // several slots: split the index
+                            j = local / co;
+                            q = nth_bit64(Mo, local - j * co);
+                        }
+                        qs[k] = q;
+                        arc[k] = so + j;
+                        labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
+                    }
+                    mq_relax(a, st, t, valid, arc, qs, labs, attempts, improved);
+                }
+                p = stop;
+                i0 += 32;
             }
         }
+        unsigned long long tm3 = first ? gtimer() : 0;
         seg_flush(st, t, ctl, a.n);
         if (first) ctl->stop_req = (a.yield && a.doorbell) ? *(volatile const uint32_t *)a.doorbell : 0u;
         if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
+        if (first) {
+            unsigned long long tm4 = gtimer();
+            ctl->t_part[0] += tm1 - tm0;
+            ctl->t_part[1] += tm2 - tm1;
+            ctl->t_part[2] += tm3 - tm2;
+            ctl->t_part[3] += tm4 - tm3;
+            ctl->items_total += n_items;
+            ctl->pairs_total += st.W;
+        }
         ++it;
         ++iters;
 
@@ -383,11 +412,12 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
         infl &= ~conv;
         conv_total |= conv;
         if (!infl) { reason = 1; break; }
-        if (a.yield && conv_total) { reason = 2; break; }
+        if (a.yield && (uint32_t)popc64(conv_total) >= a.yield) { reason = 2; break; }
         if (a.yield && ldcg_u32(&ctl->stop_req)) { reason = 3; break; }
         if (iters >= a.max_iters) { reason = 4; break; }
         if (!S) continue;
 
+        unsigned long long tm5 = first ? gtimer() : 0;
         // Split the far pile for the slots in S.  A barrier first: every
         // block has read the decision inputs before the split appends to
         // them.  Near pushes go to this iteration's queue (slot it % 3).
@@ -466,6 +496,7 @@ __global__ void __launch_bounds__(256) mq_sssp_kernel(MqArgs a) {
         if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = st.Tnew[threadIdx.x];
         __syncthreads();
         fc ^= 1;
+        if (first) ctl->t_part[4] += gtimer() - tm5;
     }
     if (!infl && reason == 0) reason = 1;
 #pragma unroll
@@ -727,7 +758,7 @@ cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uin
 }
 
 cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
-                           uint32_t max_iters, bool yield, const uint32_t *doorbell,
+                           uint32_t max_iters, uint32_t yield, const uint32_t *doorbell,
                            cudaStream_t s) {
     MqArgs a;
     a.row_ptr = g.row_ptr;
@@ -750,7 +781,7 @@ cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t d
     a.delta = delta;
     a.base_near = m.base_near;
     a.max_iters = max_iters;
-    a.yield = yield ? 1u : 0u;
+    a.yield = yield;
     cudaError_t e = cudaMemsetAsync(&m.ctl->bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;
     if (blocks > MQ_MAX_BLOCKS) blocks = MQ_MAX_BLOCKS;

@@ -35,6 +35,11 @@ struct MqControl {
     uint32_t iterations;                // iterations run by the last launch
     unsigned long long relax_attempts;
     unsigned long long relax_improved;
+    // block 0's time in each part of an iteration (ns, accumulated): masks +
+    // prefix sums, barrier after them, relaxation, flush + barrier, split
+    unsigned long long t_part[5];
+    unsigned long long items_total;     // frontier items visited
+    unsigned long long pairs_total;     // (arc, slot) pairs relaxed
 };
 
 struct MqState {
@@ -70,11 +75,11 @@ cudaError_t mq_launch_clear(const DevGraph &g, MqState &m, unsigned long long ma
                             cudaStream_t s);
 cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uint32_t delta,
                            cudaStream_t s);
-// Runs the persistent multi-query SSSP.  yield: return when a slot converges
-// or *doorbell (host-mapped) is set; otherwise run until every in-flight slot
-// converged.  max_iters caps this launch.
+// Runs the persistent multi-query SSSP.  yield > 0: return once `yield`
+// slots converged or *doorbell (host-mapped) is set; yield = 0: run until
+// every in-flight slot converged.  max_iters caps this launch.
 cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
-                           uint32_t max_iters, bool yield, const uint32_t *doorbell,
+                           uint32_t max_iters, uint32_t yield, const uint32_t *doorbell,
                            cudaStream_t s);
 // Predecessors and per-slot bridge tables for the slots in `slots`.
 cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slots,

@@ -57,9 +57,8 @@ struct BatchEngine {
     uint64_t budget = ~0ull, used = 0, fixed = 0;
     uint64_t total_iterations = 0;
     uint64_t iteration_cap = 1ull << 24;
-    // Band width of the shared frontier.  Iterations are shared by all slots,
-    // so a narrower band than the single-query default (closer to Dijkstra
-    // order, fewer wasted relaxations) pays off; 0 = a quarter of it.
+    // Band width of every slot's near/far threshold (0 = the graph's
+    // single-query default).
     uint32_t batch_delta = 0;
     // cumulative wall time (ms) and counters, for tracing
     double ms_sssp = 0, ms_scan = 0, ms_tail = 0, ms_admit = 0;
@@ -85,7 +84,7 @@ struct BatchEngine {
         int per_sm = mq_occupancy(256);
         int sms = api_geometry(G).sm_count;
         blocks = std::max(1, per_sm) * sms;
-        delta = batch_delta ? batch_delta : std::max<uint32_t>(1, api_delta(G) / 4);
+        delta = batch_delta ? batch_delta : api_delta(G);
         fixed = (uint64_t)g.n * MQ_SLOTS * 12;
         ready = true;
         return STEINER_OK;
@@ -194,6 +193,9 @@ struct BatchEngine {
 
     // Runs the persistent kernel; returns the newly converged slots in
     // *done (slots stopped by an error are reported in *failed with *why).
+    // yield: leave the kernel early (retire converged slots, admit waiting
+    // queries).  It leaves once an eighth of the in-flight slots converged,
+    // so the retirement scan is shared by several slots.
     int run(bool yield, unsigned long long *done, unsigned long long *failed, int *why) {
         cudaStream_t s = api_stream(G);
         *done = *failed = 0;
@@ -206,7 +208,9 @@ struct BatchEngine {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&m.ctl->converged, &h_masks[1], 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = mq_launch_sssp(api_graph(G), m, blocks, delta, 1u << 20, yield, doorbell_dev, s);
+            e = mq_launch_sssp(api_graph(G), m, blocks, delta, 1u << 20,
+                               yield ? std::max(1, __builtin_popcountll(inflight) / 8) : 0,
+                               doorbell_dev, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_ctl, m.ctl, sizeof(MqControl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -318,6 +322,9 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_iterations") return (int64_t)B->iterations_run;
     if (k == "batch_relax_attempts") return (int64_t)B->relax_attempts;
     if (k == "batch_delta") return B->delta;
+    if (k.rfind("batch_t", 0) == 0 && k.size() == 8 && B->h_ctl) return (int64_t)B->h_ctl->t_part[k[7] - '0'];
+    if (k == "batch_items" && B->h_ctl) return (int64_t)B->h_ctl->items_total;
+    if (k == "batch_pairs" && B->h_ctl) return (int64_t)B->h_ctl->pairs_total;
     if (k == "batch_reset") {
         B->ms_sssp = B->ms_scan = B->ms_tail = B->ms_admit = 0;
         B->launches = B->iterations_run = 0;
@@ -338,7 +345,7 @@ static BatchEngine *engine_of(steiner_graph *G) {
 int batch_set_delta(steiner_graph *G, uint32_t d) {
     BatchEngine *B = engine_of(G);
     B->batch_delta = d;
-    if (B->ready) B->delta = d ? d : std::max<uint32_t>(1, api_delta(G) / 4);
+    if (B->ready) B->delta = d ? d : api_delta(G);
     return STEINER_OK;
 }
 

@@ -209,6 +209,8 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
             }
         }
     }
+    // rounds that improve nothing skip the append machinery
+    if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
     bool to_near[ILP], to_far[ILP];
     uint32_t deg[ILP];
 #pragma unroll
@@ -237,7 +239,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
 // the persistent near/far kernel
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) sssp_kernel(SsspArgs a) {
+__global__ void __launch_bounds__(256, 4) sssp_kernel(SsspArgs a) {
     __shared__ Stage st;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;

@@ -189,9 +189,10 @@ def steiner_query_detail(h: int, seeds, pairs: bool = True) -> Result:
     n = int(npairs.value)
     if pp:
         arr = np.zeros((n, 5), np.uint64)
-        for i in range(n):
-            p = pp[i]
-            arr[i] = (p.ra, p.rb, p.b, p.arc, p.in_mst)
+        if n:
+            rec = np.ctypeslib.as_array(pp, shape=(n,))
+            for i, f in enumerate(("ra", "rb", "b", "arc", "in_mst")):
+                arr[:, i] = rec[f]
         lib.steiner_pairs_free(pp)
         out.pairs = arr
     out.stats = {f: getattr(st, f) for f, _ in steiner_stats_t._fields_}

@@ -67,3 +67,13 @@ def test_kernels_compile_for_sm103a():
     from paper_2205_14503_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
     assert os.path.exists(build.build())
+
+
+def test_autotune_fingerprint_is_stable_and_sensitive():
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import autotune
+    a = wl.grid(50, 40, 100, seed=1)
+    b = wl.grid(50, 40, 100, seed=1)
+    c = wl.grid(50, 40, 100, seed=2)
+    assert autotune.fingerprint(a) == autotune.fingerprint(b)
+    assert autotune.fingerprint(a) != autotune.fingerprint(c)

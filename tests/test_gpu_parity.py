@@ -212,3 +212,23 @@ def test_iteration_cap_reports_timeout():
         res = Gd.query([0, 4999])
     ref = oracle.steiner(g, [0, 4999], want_labels=False)
     assert res.status == st.STEINER_OK and res.total == ref.total
+
+
+def test_autotuner_changes_time_not_results(tmp_path):
+    from paper_2205_14503_gb300 import autotune
+    g = wl.grid(300, 300, 1000, seed=5)
+    seeds = G.seeds_from(np.arange(g.n), 20, 5)
+    ref = oracle.steiner(g, seeds, want_labels=False)
+    cache = str(tmp_path / "tune.json")
+    with st.SteinerGraph(g) as Gd:
+        entry = autotune.tune(Gd, g, [seeds], delta_factors=(0.5, 2), block_fractions=(0.5, 1.0),
+                              reps=1, cache_path=cache)
+        assert Gd.get_param("delta") == entry["delta"]
+        assert Gd.get_param("sssp_blocks") == entry["sssp_blocks"]
+        res = Gd.query(seeds)
+    assert np.array_equal(res.edges, ref.edges) and res.total == ref.total
+    with st.SteinerGraph(g) as Gd:
+        assert autotune.apply_cached(Gd, g, cache) == entry
+        assert Gd.get_param("sssp_blocks") == entry["sssp_blocks"]
+        res = Gd.query(seeds)
+    assert np.array_equal(res.edges, ref.edges)
