@@ -235,7 +235,14 @@ def run_ours(args, world, rank, local):
     G = st.SteinerGraph(g, device=local)
     load_s = time.perf_counter() - t0
     tuned = None
-    if not args.no_autotune:
+    if args.tuned:
+        # explicit (delta, blocks, local rounds), e.g. for profiling captures
+        d, b, lr = (int(x) for x in args.tuned.split(","))
+        G.set_param("delta", d)
+        G.set_param("sssp_blocks", b)
+        G.set_param("local_rounds", lr)
+        tuned = {"delta": d, "sssp_blocks": G.get_param("sssp_blocks"), "local_rounds": lr}
+    elif not args.no_autotune:
         # set-up, untimed: band width and persistent grid size for this graph
         from paper_2205_14503_gb300 import autotune
         tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
@@ -311,6 +318,7 @@ def run_ours(args, world, rank, local):
                  "work_efficiency": stats["relax_attempts"] / m_arcs,
                  "delta": tuned["delta"] if tuned else None,
                  "blocks": tuned["sssp_blocks"] if tuned else None,
+                 "local_rounds": tuned["local_rounds"] if tuned else None,
                  "autotuned": bool(tuned)},
         "tree": {"edges": int(res.edges.shape[0]), "total": int(res.total)},
         "graph_load_s": load_s,
@@ -457,6 +465,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default band width and grid size")
+    ap.add_argument("--tuned", default=None,
+                    help="DELTA,BLOCKS,LOCAL_ROUNDS instead of autotuning (BLOCKS 0 = all)")
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")

@@ -184,10 +184,20 @@ int steiner_serve_stop(steiner_graph_t g);
 
 /*
  * Tuning parameters of a graph handle (used by the autotuner):
- *   "delta"      near/far band width of the Voronoi phase (>= 1)
- *   "max_iters"  frontier iteration cap (STEINER_ETIMEOUT beyond it)
- * steiner_get_param also reads "sssp_blocks", "sm_count" and
- * "heavy_chunks"; it returns -1 for an unknown key.
+ *   "delta"        near/far band width of the Voronoi phase (>= 1)
+ *   "sssp_blocks"  blocks of the persistent Voronoi kernel (0 = every
+ *                  co-resident block; at most "sssp_max_blocks")
+ *   "local_rounds" block-local relaxation rounds per frontier iteration
+ *                  (0 = off): a block keeps relaxing the vertices it just
+ *                  queued, a hop per round, before the grid barrier
+ *   "batch_delta"  band width of the multi-query engine (0 = "delta")
+ *   "max_iters"    frontier iteration cap (STEINER_ETIMEOUT beyond it)
+ * steiner_get_param also reads "sssp_max_blocks", "sm_count",
+ * "heavy_chunks" and the multi-query engine's tracing counters
+ * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
+ * microseconds, "batch_launches", "batch_iterations", "batch_items",
+ * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds; "batch_reset"
+ * clears the timers).  It returns -1 for an unknown key.
  */
 int steiner_set_param(steiner_graph_t g, const char *key, int64_t value);
 int64_t steiner_get_param(steiner_graph_t g, const char *key);

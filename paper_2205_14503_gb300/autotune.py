@@ -1,11 +1,12 @@
 """Autotuner for the Voronoi (SSSP) phase.
 
-The near/far band width ``delta`` and the persistent kernel's grid size
-trade iterations against wasted relaxations and barrier cost, and the best
-point depends on the graph: a high-diameter grid is latency-bound (fewer
-blocks make each grid barrier cheaper, a wide band saves iterations), a
-scale-free graph is throughput-bound (all co-resident blocks, a band near
-the default).  ``tune`` tries a small grid of both on sample queries, timing
+The near/far band width ``delta``, the persistent kernel's grid size and
+the number of block-local relaxation rounds per iteration trade iterations
+against wasted relaxations and barrier cost, and the best point depends on
+the graph: a high-diameter grid is latency-bound (block-local rounds carry
+the wavefront several hops per grid barrier), a scale-free graph is
+throughput-bound (no local rounds, all co-resident blocks, a band near the
+default).  ``tune`` tries a small grid of both on sample queries, timing
 the Voronoi kernel with the library's own CUDA events, applies the fastest
 and caches it in a JSON file keyed by a fingerprint of the graph and the GPU
 name, so later handles of the same graph start tuned (``apply_cached``).
@@ -64,14 +65,16 @@ def apply_cached(G: "st.SteinerGraph", graph, cache_path: str = DEFAULT_CACHE,
         return None
     G.set_param("delta", entry["delta"])
     G.set_param("sssp_blocks", min(entry["sssp_blocks"], G.get_param("sssp_max_blocks")))
+    G.set_param("local_rounds", entry.get("local_rounds", 0))
     return entry
 
 
-def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.5, 1, 2, 4),
-         block_fractions=(0.25, 0.5, 0.75, 1.0), reps: int = 2,
+def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.5, 1, 2),
+         block_fractions=(0.5, 1.0), local_rounds=(0, 32), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
-    """Times the Voronoi kernel over a grid of (delta, blocks) on the sample
-    seed sets, applies the fastest and (optionally) caches it."""
+    """Times the Voronoi kernel over a grid of (delta, blocks, block-local
+    rounds) on the sample seed sets, applies the fastest and (optionally)
+    caches it."""
     d0 = G.get_param("delta")
     bmax = G.get_param("sssp_max_blocks")
     sm = max(1, G.get_param("sm_count"))
@@ -79,25 +82,29 @@ def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.5, 1, 2, 4)
     for fb in block_fractions:
         blocks = max(sm, int(round(bmax * fb / sm)) * sm)
         blocks = min(blocks, bmax)
-        for fd in delta_factors:
-            delta = max(1, int(round(d0 * fd)))
-            G.set_param("delta", delta)
-            G.set_param("sssp_blocks", blocks)
-            ms = 0.0
-            for _ in range(reps):
-                for seeds in sample_seeds:
-                    r = G.query_detail(seeds, pairs=False)
-                    if r.status not in (st.STEINER_OK, st.STEINER_EDISCONNECTED):
-                        raise st.SteinerError(r.status, st.last_error())
-                    ms += r.stats["ms_voronoi"]
-            trials.append((ms / reps, delta, blocks))
+        for lr in local_rounds:
+            for fd in delta_factors:
+                delta = max(1, int(round(d0 * fd)))
+                G.set_param("delta", delta)
+                G.set_param("sssp_blocks", blocks)
+                G.set_param("local_rounds", lr)
+                ms = 0.0
+                for _ in range(reps):
+                    for seeds in sample_seeds:
+                        r = G.query_detail(seeds, pairs=False)
+                        if r.status not in (st.STEINER_OK, st.STEINER_EDISCONNECTED):
+                            raise st.SteinerError(r.status, st.last_error())
+                        ms += r.stats["ms_voronoi"]
+                trials.append((ms / reps, delta, blocks, lr))
     trials.sort()
-    best_ms, delta, blocks = trials[0]
+    best_ms, delta, blocks, lr = trials[0]
     G.set_param("delta", delta)
     G.set_param("sssp_blocks", blocks)
-    entry = {"delta": delta, "sssp_blocks": blocks, "ms_voronoi": best_ms,
+    G.set_param("local_rounds", lr)
+    entry = {"delta": delta, "sssp_blocks": blocks, "local_rounds": lr, "ms_voronoi": best_ms,
              "default_delta": d0, "max_blocks": bmax,
-             "trials": [{"ms": t, "delta": d, "blocks": b} for t, d, b in trials]}
+             "trials": [{"ms": t, "delta": d, "blocks": b, "local_rounds": r}
+                        for t, d, b, r in trials]}
     if cache_path:
         cache = _load(cache_path)
         cache[_key(graph, device)] = entry

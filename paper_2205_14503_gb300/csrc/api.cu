@@ -68,6 +68,7 @@ struct steiner_graph {
     uint32_t nbits = 1;
     uint32_t delta = 0;
     uint32_t max_iters = 1u << 22;
+    uint32_t local_rounds = 0;
     Control *h_ctl = nullptr;      // pinned
     cudaEvent_t ev[6] = {};
     BatchEngine *batch = nullptr;
@@ -191,7 +192,7 @@ int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, fl
     Workspace &ws = G->ws;
     cudaStream_t s = G->stream;
     CK(cudaMemcpyAsync(ws.seeds, ss.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s));
-    SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far};
+    SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds};
     CK(cudaEventRecord(G->ev[0], s));
     CK(launch_init(G->g, ws, k, s));
     CK(cudaEventRecord(G->ev[1], s));
@@ -475,6 +476,9 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
         int maxb = G->geo.sssp_max_blocks;
         if (value < 0 || value > maxb) return fail(STEINER_EINVAL, "sssp_blocks out of range");
         G->geo.sssp_blocks = value ? (int)value : maxb;
+    } else if (!strcmp(key, "local_rounds")) {
+        if (value < 0 || value > 1024) return fail(STEINER_EINVAL, "local_rounds out of range");
+        G->local_rounds = (uint32_t)value;
     } else if (!strcmp(key, "max_iters")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "max_iters out of range");
         G->max_iters = (uint32_t)value;
@@ -488,6 +492,7 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!G || !key) return -1;
     if (!strcmp(key, "delta")) return G->delta;
     if (!strcmp(key, "max_iters")) return G->max_iters;
+    if (!strcmp(key, "local_rounds")) return G->local_rounds;
     if (!strcmp(key, "sssp_blocks")) return G->geo.sssp_blocks;
     if (!strcmp(key, "sssp_max_blocks")) return G->geo.sssp_max_blocks;
     if (!strcmp(key, "sm_count")) return G->geo.sm_count;

@@ -35,6 +35,7 @@ struct SsspArgs {
     uint32_t base_near;
     uint32_t base_far;
     uint32_t heavy_cap;
+    uint32_t local_rounds;   // block-local relaxation rounds per iteration (0 = off)
 };
 
 // ---------------------------------------------------------------------------
@@ -82,7 +83,7 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const in
 // ---------------------------------------------------------------------------
 
 constexpr int ILP = 4;                 // arcs per lane per round group
-constexpr uint32_t NEAR_STAGE = 2048;  // block staging capacity (near items)
+constexpr uint32_t NEAR_STAGE = 4096;  // block staging capacity (near items)
 constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
 
 // Where the appends of one processing segment go.
@@ -108,6 +109,7 @@ struct Stage {
     uint32_t far_buf[FAR_STAGE];
     uint32_t near_n, far_n, far_min;
     uint32_t base_near, base_far;
+    uint32_t local_lo;      // near_buf[0, local_lo) was relaxed by this block already
 };
 
 __device__ __forceinline__ void stage_reset(Stage &st) {
@@ -115,6 +117,7 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
         st.near_n = 0;
         st.far_n = 0;
         st.far_min = INF32;
+        st.local_lo = 0;
     }
     __syncthreads();
 }
@@ -125,7 +128,9 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
 __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uint32_t n,
                                             uint32_t *err) {
     __syncthreads();
+    uint32_t lo = st.local_lo;
     uint32_t nn = min(st.near_n, NEAR_STAGE), nf = min(st.far_n, FAR_STAGE);
+    nn = nn > lo ? nn - lo : 0;
     if (threadIdx.x == 0) {
         st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
         st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
@@ -134,7 +139,7 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
         uint32_t slot = st.base_near + i;
-        if (slot < n) t.qn[slot] = st.near_buf[i];
+        if (slot < n) t.qn[slot] = st.near_buf[lo + i];
         else atomicOr(err, ERR_CAPACITY);
     }
     for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -222,6 +227,10 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         uint32_t v = e[u].x;
         if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];   // independent of the exchange
+            // with block-local rounds a staged vertex may be relaxed this very
+            // iteration: publish the label before reading its stamp (the
+            // local reader resets the stamp, fences, then reads the label)
+            if (a.local_rounds) __threadfence();
             to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
@@ -239,7 +248,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
 // the persistent near/far kernel
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256, 4) sssp_kernel(SsspArgs a) {
+__global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     __shared__ Stage st;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -337,6 +346,56 @@ __global__ void __launch_bounds__(256, 4) sssp_kernel(SsspArgs a) {
                         arc[q] = so + (j - eo);
                     }
                     relax_group(a, st, t, valid, arc, labs, bsz == 32, attempts, improved);
+                }
+            }
+        }
+        // Block-local rounds: relax the vertices this block just staged for
+        // the next iteration right away, a hop further per round, instead
+        // of waiting for the grid barrier; what is left is flushed.
+        if (a.local_rounds) {
+            const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+            const uint32_t tag_cur = t.tag_next - 1;
+            for (uint32_t r = 0; r < a.local_rounds; ++r) {
+                __syncthreads();
+                const uint32_t lo = st.local_lo, hi = min(st.near_n, NEAR_STAGE);
+                __syncthreads();
+                if (lo >= hi) break;
+                if (threadIdx.x == 0) st.local_lo = hi;
+                const uint32_t cnt = hi - lo;
+                const uint32_t lper = (cnt + nwb - 1) / nwb;
+                const uint32_t lbsz = lper <= 1 ? 1 : lper <= 2 ? 2 : lper <= 4 ? 4 : lper <= 8 ? 8 : lper <= 16 ? 16 : 32;
+                for (uint32_t b0 = wib * lbsz; b0 < cnt; b0 += nwb * lbsz) {
+                    uint32_t i = lo + b0 + lane;
+                    bool has = lane < lbsz && b0 + lane < cnt;
+                    uint32_t s = 0, deg = 0;
+                    uint64_t lab = INF64;
+                    if (has) {
+                        uint32_t u = st.near_buf[i];
+                        atomicExch(&a.stamp_near[u], tag_cur);     // later improvements re-push u
+                        __threadfence();
+                        s = a.row_ptr[u];
+                        deg = a.row_ptr[u + 1] - s;
+                        lab = ldcg_u64(&a.label[u]);
+                    }
+                    uint32_t incl = warp_inclusive_scan(deg);
+                    uint32_t excl = incl - deg;
+                    uint32_t total = __shfl_sync(FULL, incl, 31);
+                    for (uint32_t b = 0; b < total; b += 32 * ILP) {
+                        bool valid[ILP];
+                        uint32_t arc[ILP];
+                        uint64_t labs[ILP];
+#pragma unroll
+                        for (int q = 0; q < ILP; ++q) {
+                            uint32_t j = b + lane + 32 * q;
+                            valid[q] = j < total;
+                            uint32_t owner = warp_owner_search(excl, valid[q] ? j : 0);
+                            uint32_t so = __shfl_sync(FULL, s, owner);
+                            uint32_t eo = __shfl_sync(FULL, excl, owner);
+                            labs[q] = __shfl_sync(FULL, lab, owner);
+                            arc[q] = so + (j - eo);
+                        }
+                        relax_group(a, st, t, valid, arc, labs, false, attempts, improved);
+                    }
                 }
             }
         }
@@ -520,6 +579,7 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.base_near = p.base_near;
     a.base_far = p.base_far;
     a.heavy_cap = g.heavy_chunk_cap;
+    a.local_rounds = p.local_rounds;
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(geo.sssp_blocks),
                                        dim3(geo.threads), args, 0, s);

@@ -186,14 +186,17 @@ def test_voronoi_into_device_tensors():
     np.testing.assert_array_equal(pred.cpu().numpy(), ref.pred)
 
 
-@pytest.mark.parametrize("delta", [1, 7, 100, 5000, 10 ** 8])
-def test_result_is_independent_of_delta(delta):
-    """The near/far band width changes the schedule, never the fixed point."""
+@pytest.mark.parametrize("delta,local", [(1, 0), (7, 0), (100, 0), (5000, 0), (10 ** 8, 0),
+                                         (7, 4), (100, 32), (5000, 2)])
+def test_result_is_independent_of_delta(delta, local):
+    """The near/far band width and the block-local rounds change the
+    schedule, never the fixed point."""
     g = wl.rmat(13, 16, wmax=1000, seed=6)
     seeds = wl.sample_distinct(wl.largest_cc(g), 64, 6)
     ref = oracle.steiner(g, seeds)
     with st.SteinerGraph(g) as Gd:
         Gd.set_param("delta", delta)
+        Gd.set_param("local_rounds", local)
         rc, cell, dist, pred = Gd.voronoi(seeds)
         res = Gd.query(seeds)
     np.testing.assert_array_equal(cell, ref.cell)
@@ -222,7 +225,7 @@ def test_autotuner_changes_time_not_results(tmp_path):
     cache = str(tmp_path / "tune.json")
     with st.SteinerGraph(g) as Gd:
         entry = autotune.tune(Gd, g, [seeds], delta_factors=(0.5, 2), block_fractions=(0.5, 1.0),
-                              reps=1, cache_path=cache)
+                              local_rounds=(0, 8), reps=1, cache_path=cache)
         assert Gd.get_param("delta") == entry["delta"]
         assert Gd.get_param("sssp_blocks") == entry["sssp_blocks"]
         res = Gd.query(seeds)
@@ -232,3 +235,20 @@ def test_autotuner_changes_time_not_results(tmp_path):
         assert Gd.get_param("sssp_blocks") == entry["sssp_blocks"]
         res = Gd.query(seeds)
     assert np.array_equal(res.edges, ref.edges)
+
+
+@pytest.mark.parametrize("local", [1, 4, 64])
+def test_block_local_rounds_on_grids(local):
+    """High-diameter graphs are where block-local rounds run many hops."""
+    for side, k, wmax in [(200, 9, 1000), (150, 40, 1), (300, 5, 3)]:
+        g = wl.grid(side, side, wmax, seed=side + local)
+        seeds = G.seeds_from(np.arange(g.n), k, side)
+        ref = oracle.steiner(g, seeds, want_labels=True)
+        with st.SteinerGraph(g) as Gd:
+            Gd.set_param("local_rounds", local)
+            rc, cell, dist, pred = Gd.voronoi(seeds)
+            res = Gd.query(seeds)
+        np.testing.assert_array_equal(cell, ref.cell)
+        np.testing.assert_array_equal(dist, ref.dist)
+        np.testing.assert_array_equal(pred, ref.pred)
+        np.testing.assert_array_equal(res.edges, ref.edges)
