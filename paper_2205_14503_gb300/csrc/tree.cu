@@ -126,6 +126,10 @@ __device__ __forceinline__ void emit_edge(uint32_t a, uint32_t b, uint32_t w, ui
     wout[slot] = w;
 }
 
+// Two threads per MST pair: thread 0 emits the bridge and walks pred() from
+// the bridge's tail, thread 1 walks from its head.  Per hop the mark exchange
+// and the pred load are issued together, so a hop costs two dependent loads
+// (pred arc, then the arc's record) instead of three.
 __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
                               uint32_t n, const uint32_t *__restrict__ e_arc,
                               const uint32_t *__restrict__ e_mst,
@@ -133,24 +137,25 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
                               uint32_t *mark, uint32_t tag, uint32_t nbits, uint64_t *key,
                               uint32_t *wout, uint32_t cap, Control *ctl) {
     const uint32_t E = ldcg_u32(&ctl->n_pairs);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < E; j += gridDim.x * blockDim.x) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * E; t += gridDim.x * blockDim.x) {
+        const uint32_t j = t >> 1, side = t & 1;
         if (!e_mst[j]) continue;
-        atomicAdd(&ctl->n_mst, 1u);
         uint32_t arc = e_arc[j];
-        uint32_t v = arc_owner(row_ptr, n, arc);
         uint2 e = adj[arc];
-        emit_edge(v, e.x, e.y, nbits, key, wout, cap, ctl);
-        uint32_t ends[2] = {v, e.x};
-        for (int side = 0; side < 2; ++side) {
-            uint32_t x = ends[side];
-            for (uint32_t steps = 0; steps < n; ++steps) {
-                uint32_t pa = pred_arc[(uint64_t)x * pred_stride];
-                if (pa == SEED_ARC || pa == INF32) break;
-                if (atomicExch(&mark[x], tag) == tag) break;   // rest of the chain is taken
-                uint2 pe = adj[pa];
-                emit_edge(x, pe.x, pe.y, nbits, key, wout, cap, ctl);
-                x = pe.x;
-            }
+        uint32_t x = e.x;
+        if (side == 0) {
+            atomicAdd(&ctl->n_mst, 1u);
+            x = arc_owner(row_ptr, n, arc);
+            emit_edge(x, e.x, e.y, nbits, key, wout, cap, ctl);
+        }
+        for (uint32_t steps = 0; steps < n; ++steps) {
+            uint32_t pa = pred_arc[(uint64_t)x * pred_stride];
+            if (pa == SEED_ARC || pa == INF32) break;
+            uint32_t old = atomicExch(&mark[x], tag);
+            uint2 pe = adj[pa];              // independent of the exchange's result
+            if (old == tag) break;           // the rest of the chain is another walker's
+            emit_edge(x, pe.x, pe.y, nbits, key, wout, cap, ctl);
+            x = pe.x;
         }
     }
 }
@@ -312,7 +317,7 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
                         uint32_t n_bits, cudaStream_t s) {
     if (k < 2) return cudaSuccess;
     uint64_t slots = (uint64_t)k * (k - 1) / 2;
-    uint32_t blocks = (uint32_t)std::min<uint64_t>((slots + 255) / 256, 152ull * 8);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>((2 * slots + 255) / 256, 152ull * 8);
     expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
                                          ws.pred_stride, ws.mark, tag, n_bits, ws.tree_key,
                                          ws.tree_w, ws.tree_cap, ws.ctl);
