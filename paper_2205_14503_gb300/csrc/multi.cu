@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         }
         unsigned long long tm3 = first ? gtimer() : 0;
         seg_flush(st, t, ctl, a.n);
-        if (first) ctl->stop_req = (a.yield && a.doorbell) ? *(volatile const uint32_t *)a.doorbell : 0u;
+        if (first)
+            ctl->stop_req[it & 1] = (a.yield && a.doorbell) ? *(volatile const uint32_t *)a.doorbell : 0u;
         if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }
         if (first) {
             unsigned long long tm4 = gtimer();
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         conv_total |= conv;
         if (!infl) { reason = 1; break; }
         if (a.yield && (uint32_t)popc64(conv_total) >= a.yield) { reason = 2; break; }
-        if (a.yield && ldcg_u32(&ctl->stop_req)) { reason = 3; break; }
+        if (a.yield && ldcg_u32(&ctl->stop_req[(it - 1) & 1])) { reason = 3; break; }
         if (iters >= a.max_iters) { reason = 4; break; }
         if (!S) continue;
 

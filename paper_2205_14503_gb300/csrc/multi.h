@@ -21,7 +21,10 @@ struct MqControl {
     uint32_t err;                 // ERR_* (global)
     uint32_t it;                  // next iteration (persists across launches)
     uint32_t fc;                  // far pile being filled
-    uint32_t stop_req;            // published by block 0 before each barrier
+    // doorbell as seen by block 0 before the barrier that ends iteration i,
+    // at stop_req[i & 1] (two copies: a slow block still reading one copy
+    // never sees block 0 overwrite it with the next iteration's)
+    uint32_t stop_req[2];
     uint32_t near_count[3];
     uint32_t far_count[2];
     unsigned long long act[3];    // slots with near work queued, per iteration slot
