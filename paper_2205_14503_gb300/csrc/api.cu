@@ -86,6 +86,9 @@ int ensure_n_workspace(steiner_graph *G) {
     CK(dalloc(ws.pred_arc, n));
     CK(dalloc(ws.stamp_near, n));
     CK(dalloc(ws.stamp_far, n));
+    CK(dalloc(ws.stamp_band, n));
+    CK(dalloc(ws.band_q, n));
+    CK(dalloc(ws.band_hq, G->g.heavy_chunk_cap));
     CK(dalloc(ws.mark, n));
     CK(dalloc(ws.q[0], n));
     CK(dalloc(ws.q[1], n));
@@ -102,8 +105,9 @@ int ensure_n_workspace(steiner_graph *G) {
     ws.tree_cap = (uint32_t)tcap;
     CK(cudaMemsetAsync(ws.stamp_near, 0, (size_t)n * 4, G->stream));
     CK(cudaMemsetAsync(ws.stamp_far, 0, (size_t)n * 4, G->stream));
+    CK(cudaMemsetAsync(ws.stamp_band, 0, (size_t)n * 4, G->stream));
     CK(cudaMemsetAsync(ws.mark, 0, (size_t)n * 4, G->stream));
-    ws.epoch_near = ws.epoch_far = ws.epoch_mark = 1;
+    ws.epoch_near = ws.epoch_far = ws.epoch_mark = ws.epoch_band = 1;
     G->ws_ready = true;
     return STEINER_OK;
 }
@@ -173,11 +177,14 @@ void advance_epochs(Workspace &ws, const Control &c, cudaStream_t s) {
     ws.epoch_near += c.iterations + 2;
     ws.epoch_far += c.phases + 2;
     ws.epoch_mark += 1;
-    if (c.err != 0 || ws.epoch_near > 0x7FFFFFFFu || ws.epoch_far > 0x7FFFFFFFu || ws.epoch_mark > 0x7FFFFFFFu) {
+    ws.epoch_band += c.bands + 2;
+    if (c.err != 0 || ws.epoch_near > 0x7FFFFFFFu || ws.epoch_far > 0x7FFFFFFFu ||
+        ws.epoch_mark > 0x7FFFFFFFu || ws.epoch_band > 0x7FFFFFFFu) {
         cudaMemsetAsync(ws.stamp_near, 0, (size_t)ws.n * 4, s);
         cudaMemsetAsync(ws.stamp_far, 0, (size_t)ws.n * 4, s);
+        cudaMemsetAsync(ws.stamp_band, 0, (size_t)ws.n * 4, s);
         cudaMemsetAsync(ws.mark, 0, (size_t)ws.n * 4, s);
-        ws.epoch_near = ws.epoch_far = ws.epoch_mark = 1;
+        ws.epoch_near = ws.epoch_far = ws.epoch_mark = ws.epoch_band = 1;
     }
 }
 
@@ -192,7 +199,8 @@ int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, fl
     Workspace &ws = G->ws;
     cudaStream_t s = G->stream;
     CK(cudaMemcpyAsync(ws.seeds, ss.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s));
-    SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds};
+    SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
+                 ws.epoch_band};
     CK(cudaEventRecord(G->ev[0], s));
     CK(launch_init(G->g, ws, k, s));
     CK(cudaEventRecord(G->ev[1], s));
@@ -385,13 +393,13 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
         cudaFree(d_col);
         return bail(cuda_fail(e, "cudaMalloc"));
     }
-    if ((e = dalloc(d_bad, 1)) != cudaSuccess) {
+    if ((e = dalloc(d_bad, 2)) != cudaSuccess) {
         cudaFree(d_col);
         cudaFree(d_w);
         return bail(cuda_fail(e, "cudaMalloc"));
     }
     cudaStream_t s = G->stream;
-    uint32_t bad = 0;
+    uint32_t bad[2] = {0, 0};     // flags, largest weight
     e = cudaMemcpyAsync(G->g.row_ptr, row_ptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_arcs)
         e = cudaMemcpyAsync(d_col, col, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, s);
@@ -400,20 +408,22 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
     if (e == cudaSuccess && !chunks.empty())
         e = cudaMemcpyAsync(G->g.heavy_chunks, chunks.data(), chunks.size() * 8,
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, s);
-    if (e == cudaSuccess) e = launch_validate_graph(G->g.row_ptr, d_col, d_w, n, n_arcs, G->g.adj, d_bad, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 8, s);
+    if (e == cudaSuccess)
+        e = launch_validate_graph(G->g.row_ptr, d_col, d_w, n, n_arcs, G->g.adj, d_bad, d_bad + 1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, d_bad, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_col);
     cudaFree(d_w);
     cudaFree(d_bad);
     if (e != cudaSuccess) return bail(cuda_fail(e, "graph upload"));
-    if (bad) {
+    if (bad[0]) {
         char msg[160];
         snprintf(msg, sizeof msg, "malformed graph (flags 0x%x: 1 range, 2 self-loop, 4 zero weight, "
-                 "8 unsorted/duplicate, 16 asymmetric)", bad);
+                 "8 unsorted/duplicate, 16 asymmetric)", bad[0]);
         return bail(fail(STEINER_EINVAL, msg));
     }
+    G->g.max_w = bad[1];
     // launch geometry of the persistent kernels
     cudaDeviceGetAttribute(&G->geo.sm_count, cudaDevAttrMultiProcessorCount, device);
     G->geo.threads = 256;
@@ -448,7 +458,8 @@ void steiner_free_graph(steiner_graph_t G) {
     cudaSetDevice(G->device);
     if (G->stream) cudaStreamSynchronize(G->stream);
     Workspace &ws = G->ws;
-    void *bufs[] = {ws.label, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.mark, ws.q[0], ws.q[1],
+    void *bufs[] = {ws.label, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.stamp_band, ws.band_q,
+                    ws.band_hq, ws.mark, ws.q[0], ws.q[1],
                     ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
                     ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
                     ws.best, ws.tree_key, ws.tree_key2, ws.tree_w, ws.tree_w2, G->g.row_ptr,

@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
                                                        const int32_t *__restrict__ col,
                                                        const uint32_t *__restrict__ w,
                                                        uint32_t n, uint2 *__restrict__ adj,
-                                                       uint32_t *bad) {
+                                                       uint32_t *bad, uint32_t *max_w) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    uint32_t flags = 0;
+    uint32_t flags = 0, wmax = 0;
     for (uint32_t b0 = warp * 32; b0 < n; b0 += nwarps * 32) {
         uint32_t u = b0 + lane;
         uint32_t s = 0, deg = 0;
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
             int32_t c = col[e];
             uint32_t wt = w[e];
             adj[e] = make_uint2((uint32_t)c, wt);
+            wmax = max(wmax, wt);
             if (c < 0 || (uint32_t)c >= n) {
                 flags |= BAD_RANGE;
                 continue;
@@ -69,16 +70,18 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
         }
     }
     if (flags) atomicOr(bad, flags);
+    wmax = __reduce_max_sync(FULL, wmax);
+    if (lane == 0 && wmax) atomicMax(max_w, wmax);
 }
 
 cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,
                                   uint32_t n, uint64_t m, uint2 *adj, uint32_t *bad,
-                                  cudaStream_t s) {
+                                  uint32_t *max_w, cudaStream_t s) {
     (void)m;
     uint64_t blocks = ((uint64_t)n + 255) / 256;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
     if (blocks < 1) blocks = 1;
-    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, bad);
+    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, bad, max_w);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ struct DevGraph {
     uint64_t *heavy_chunks = nullptr;   // (v << 32) | chunk index, for deg >= HEAVY_DEG
     uint32_t n_heavy_chunks = 0;
     uint32_t heavy_chunk_cap = 0;   // bound on chunk entries a frontier can hold
+    uint32_t max_w = 0;             // largest arc weight
 };
 
 constexpr int TRACE_LEN = 64;
@@ -48,6 +49,11 @@ struct Control {
     GridBarrier bar2;
     uint32_t mst_any;
     uint32_t exit_reason;        // 1 converged, 2 iteration cap, 3/4 barrier gave up
+    // band lists of the light/heavy arc split: vertices relaxed in the
+    // current band (light items, heavy-row chunks) and the passes run
+    uint32_t band_count;
+    uint32_t band_hcount;
+    uint32_t bands;
     uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
 };
 
@@ -59,6 +65,9 @@ struct Workspace {
     uint32_t pred_stride = 1;       // pred of v at pred_arc[v * pred_stride]
     uint32_t *stamp_near = nullptr;
     uint32_t *stamp_far = nullptr;
+    uint32_t *stamp_band = nullptr;  // band-list membership tags
+    uint32_t *band_q = nullptr;      // vertices relaxed in the current band, n
+    uint64_t *band_hq = nullptr;     // their heavy-row chunks, heavy_chunk_cap
     uint32_t *mark = nullptr;       // tree-walk stamps
     uint32_t *q[2] = {nullptr, nullptr};      // light frontier
     uint64_t *hq[2] = {nullptr, nullptr};     // heavy-chunk frontier
@@ -84,7 +93,7 @@ struct Workspace {
     uint32_t *tree_w = nullptr, *tree_w2 = nullptr;
     uint32_t tree_cap = 0;
     // tags that avoid clearing the stamp arrays between queries
-    uint32_t epoch_near = 0, epoch_far = 0, epoch_mark = 0;
+    uint32_t epoch_near = 0, epoch_far = 0, epoch_mark = 0, epoch_band = 0;
 };
 
 // Launch geometry of the persistent kernels (from the occupancy API).
@@ -102,6 +111,7 @@ struct SsspParams {
     uint32_t base_near;      // first near tag of this query
     uint32_t base_far;       // first far tag of this query
     uint32_t local_rounds;   // block-local relaxation rounds per iteration
+    uint32_t base_band;      // first band-list tag of this query
 };
 
 // voronoi.cu
@@ -126,6 +136,6 @@ int mst_occupancy(int threads);
 // graph.cu
 cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col,
                                   const uint32_t *w, uint32_t n, uint64_t m, uint2 *adj,
-                                  uint32_t *bad, cudaStream_t s);
+                                  uint32_t *bad, uint32_t *max_w, cudaStream_t s);
 
 }  // namespace stn

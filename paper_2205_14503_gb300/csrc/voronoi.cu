@@ -15,6 +15,16 @@
 // parking the rest (far) until the near frontier drains, then raising T by
 // delta.  One persistent cooperative kernel runs all iterations with a
 // bounded grid barrier between them.
+//
+// Light and heavy arcs (the edge classes of delta-stepping): while a band
+// [T - delta, T) iterates, only arcs lighter than delta are relaxed, since
+// a heavier arc out of the band cannot land inside it.  Every vertex
+// relaxed in the band is listed once; when the band's frontier drains, one
+// extra pass relaxes the heavy arcs of the listed vertices with their final
+// labels, so a vertex improved several times inside its band (a hub reached
+// by many light paths) scans its heavy arcs once.  All of its proposals land
+// at or above T, in the far pile.  The split is on only when some arc
+// weight reaches delta.
 #include "internal.h"
 
 namespace stn {
@@ -36,6 +46,11 @@ struct SsspArgs {
     uint32_t base_far;
     uint32_t heavy_cap;
     uint32_t local_rounds;   // block-local relaxation rounds per iteration (0 = off)
+    uint32_t *stamp_band;    // band-list membership tags
+    uint32_t *band_q;        // vertices relaxed in the current band
+    uint64_t *band_hq;       // heavy-row chunks of listed high-degree vertices
+    uint32_t base_band;
+    uint32_t defer;          // light/heavy arc split on
 };
 
 // ---------------------------------------------------------------------------
@@ -167,11 +182,14 @@ __device__ __forceinline__ void push_near(const SsspArgs &a, Stage &st, const Pu
     }
 }
 
+// Far appends: `want` appends v to the pile (first time this phase);
+// `cand` marks every far proposal, so far_min bounds the pile from below
+// even for vertices already in it.
 __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const PushTargets &t,
-                                         bool want, uint32_t v, uint32_t d) {
+                                         bool want, bool cand, uint32_t v, uint32_t d) {
     stage_append(want, v, st.far_buf, &st.far_n, FAR_STAGE, t.farq, t.far_count, a.n, &a.ctl->err);
-    if (__any_sync(FULL, want)) {
-        uint32_t m = want ? d : INF32;
+    if (__any_sync(FULL, cand)) {
+        uint32_t m = cand ? d : INF32;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
         if (lane_id() == 0 && m != INF32) atomicMin(&st.far_min, m);
@@ -179,8 +197,9 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
 }
 
 // Relaxes up to ILP arcs per lane.  For arc u of this lane: valid[u], the
-// arc index and the tail's label.  The loads and atomics of the ILP arcs
-// are issued back to back so their latencies overlap.
+// arc index and the tail's label; only arcs with wlo <= weight < whi are
+// relaxed.  The loads and atomics of the ILP arcs are issued back to back
+// so their latencies overlap.
 // With `precheck` a plain load of the head's label comes first and only
 // improving proposals issue the atomic: right for thick frontiers, where
 // L2 atomic throughput is the limit; thin frontiers are latency-bound and
@@ -188,19 +207,22 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
 __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const PushTargets &t,
                                             const bool (&valid)[ILP], const uint32_t (&arc)[ILP],
                                             const uint64_t (&lab)[ILP], bool precheck,
+                                            uint32_t wlo, uint32_t whi,
                                             unsigned long long &attempts,
                                             unsigned long long &improved) {
     uint2 e[ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u)
+    for (int u = 0; u < ILP; ++u) {
+        e[u] = make_uint2(0, 0);
         if (valid[u]) e[u] = __ldg(&a.adj[arc[u]]);
+    }
     uint64_t nd[ILP];
     bool imp[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
         imp[u] = false;
         nd[u] = INF32;
-        if (valid[u]) {
+        if (valid[u] && e[u].y >= wlo && e[u].y < whi) {
             ++attempts;
             nd[u] = (lab[u] >> 32) + (uint64_t)e[u].y;
             // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
@@ -216,11 +238,11 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
     }
     // rounds that improve nothing skip the append machinery
     if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
-    bool to_near[ILP], to_far[ILP];
+    bool to_near[ILP], to_far[ILP], cand[ILP];
     uint32_t deg[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-        to_near[u] = to_far[u] = false;
+        to_near[u] = to_far[u] = cand[u] = false;
         deg[u] = 0;
         if (!imp[u]) continue;
         ++improved;
@@ -234,14 +256,41 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
             to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
+            cand[u] = true;
             to_far[u] = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
         }
     }
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
         push_near(a, st, t, to_near[u], e[u].x, deg[u]);
-        push_far(a, st, t, to_far[u], e[u].x, (uint32_t)nd[u]);
+        push_far(a, st, t, to_far[u], cand[u], e[u].x, (uint32_t)nd[u]);
     }
+}
+
+// Lists vertex u (lanes with `want`) in the current band once.
+__device__ __forceinline__ void band_track(const SsspArgs &a, bool want, uint32_t u, uint32_t tag) {
+    bool add = want && atomicExch(&a.stamp_band[u], tag) != tag;
+    uint32_t slot = warp_append(add, &a.ctl->band_count, a.n, &a.ctl->err);
+    if (slot != INF32) a.band_q[slot] = u;
+}
+
+// Lists high-degree vertex u (warp-uniform) in the current band once, as
+// its CHUNK-arc pieces.
+__device__ __forceinline__ void band_track_heavy(const SsspArgs &a, uint32_t u, uint32_t deg,
+                                                 uint32_t tag) {
+    const uint32_t lane = lane_id();
+    uint32_t add = 0;
+    if (lane == 0) add = atomicExch(&a.stamp_band[u], tag) != tag;
+    if (!__shfl_sync(FULL, add, 0)) return;
+    const uint32_t nc = (deg + CHUNK - 1) / CHUNK;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->band_hcount, nc);
+    base = __shfl_sync(FULL, base, 0);
+    if (base + nc > a.heavy_cap || base + nc < base) {
+        if (lane == 0) atomicOr(&a.ctl->err, ERR_CAPACITY);
+        return;
+    }
+    for (uint32_t c = lane; c < nc; c += 32) a.band_hq[base + c] = ((uint64_t)u << 32) | c;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,14 +304,21 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     Control *ctl = a.ctl;
     unsigned long long attempts = 0, improved = 0;
-    uint32_t it = 0, phase = 0;
+    uint32_t it = 0, phase = 0, bands = 0;
     uint64_t T = a.delta;
     bool first = (blockIdx.x == 0 && threadIdx.x == 0);
+    bool hp = false;               // this iteration is a band's heavy-arc pass
 
     for (;;) {
         const uint32_t cs = it % 3, ns = (it + 1) % 3;
-        uint32_t n_light = min(ldcg_u32(&ctl->near_count[cs]), a.n);
-        uint32_t n_heavy = min(ldcg_u32(&ctl->heavy_count[cs]), a.heavy_cap);
+        uint32_t n_light, n_heavy;
+        if (hp) {
+            n_light = min(ldcg_u32(&ctl->band_count), a.n);
+            n_heavy = min(ldcg_u32(&ctl->band_hcount), a.heavy_cap);
+        } else {
+            n_light = min(ldcg_u32(&ctl->near_count[cs]), a.n);
+            n_heavy = min(ldcg_u32(&ctl->heavy_count[cs]), a.heavy_cap);
+        }
         if (first) {
             ctl->near_count[(it + 2) % 3] = 0;
             ctl->heavy_count[(it + 2) % 3] = 0;
@@ -275,8 +331,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         stage_reset(st);
         const bool odd = it & 1;
-        const uint32_t *qc = odd ? a.q1 : a.q0;
-        const uint64_t *hqc = odd ? a.hq1 : a.hq0;
+        const uint32_t *qc = hp ? a.band_q : (odd ? a.q1 : a.q0);
+        const uint64_t *hqc = hp ? a.band_hq : (odd ? a.hq1 : a.hq0);
         const uint32_t fc = phase & 1;
         PushTargets t;
         t.qn = odd ? a.q0 : a.q1;
@@ -289,6 +345,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         t.tag_next = a.base_near + it + 1;
         t.tag_far = a.base_far + phase;
         t.T = T;
+        // arcs relaxed by this iteration: all; light ones while a band
+        // iterates under the split; heavy ones in the band's closing pass
+        const uint32_t wlo = hp ? a.delta : 0u;
+        const uint32_t whi = (a.defer && !hp) ? a.delta : 0xFFFFFFFFu;
+        const bool track = a.defer && !hp;
+        const uint32_t tag_band = a.base_band + bands;
 
         // Vertices per warp batch: a thin frontier is spread over all warps
         // (fewer sequential rounds per warp), a thick one packs 32 per warp.
@@ -300,9 +362,11 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 // one CHUNK of a high-degree vertex per warp
                 uint64_t item = __ldcg(reinterpret_cast<const unsigned long long *>(&hqc[wi]));
                 uint32_t u = (uint32_t)(item >> 32), c = (uint32_t)item;
-                uint32_t s = a.row_ptr[u] + c * CHUNK;
-                uint32_t e = min(a.row_ptr[u + 1], s + CHUNK);
+                uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
+                uint32_t s = r0 + c * CHUNK;
+                uint32_t e = min(r1, s + CHUNK);
                 uint64_t lab = ldcg_u64(&a.label[u]);
+                if (track && c == 0) band_track_heavy(a, u, r1 - r0, tag_band);
                 for (uint32_t b = s; b < e; b += 32 * ILP) {
                     bool valid[ILP];
                     uint32_t arc[ILP];
@@ -313,21 +377,22 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         valid[q] = arc[q] < e;
                         labs[q] = lab;
                     }
-                    relax_group(a, st, t, valid, arc, labs, true, attempts, improved);
+                    relax_group(a, st, t, valid, arc, labs, true, wlo, whi, attempts, improved);
                 }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
                 uint32_t i = (wi - n_heavy) * bsz + lane;
                 bool has = lane < bsz && i < n_light;
-                uint32_t s = 0, deg = 0;
+                uint32_t s = 0, deg = 0, u = 0;
                 uint64_t lab = INF64;
                 if (has) {
-                    uint32_t u = ldcg_u32(&qc[i]);
+                    u = ldcg_u32(&qc[i]);
                     s = a.row_ptr[u];
                     deg = a.row_ptr[u + 1] - s;
                     lab = ldcg_u64(&a.label[u]);
                     if (lab == INF64) deg = 0;
                 }
+                if (track) band_track(a, has, u, tag_band);
                 uint32_t incl = warp_inclusive_scan(deg);
                 uint32_t excl = incl - deg;
                 uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -345,14 +410,16 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         labs[q] = __shfl_sync(FULL, lab, owner);
                         arc[q] = so + (j - eo);
                     }
-                    relax_group(a, st, t, valid, arc, labs, bsz == 32, attempts, improved);
+                    relax_group(a, st, t, valid, arc, labs, bsz == 32, wlo, whi, attempts,
+                                improved);
                 }
             }
         }
         // Block-local rounds: relax the vertices this block just staged for
         // the next iteration right away, a hop further per round, instead
-        // of waiting for the grid barrier; what is left is flushed.
-        if (a.local_rounds) {
+        // of waiting for the grid barrier; what is left is flushed.  (A
+        // heavy-arc pass stages nothing near.)
+        if (a.local_rounds && !hp) {
             const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
             const uint32_t tag_cur = t.tag_next - 1;
             for (uint32_t r = 0; r < a.local_rounds; ++r) {
@@ -367,16 +434,17 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 for (uint32_t b0 = wib * lbsz; b0 < cnt; b0 += nwb * lbsz) {
                     uint32_t i = lo + b0 + lane;
                     bool has = lane < lbsz && b0 + lane < cnt;
-                    uint32_t s = 0, deg = 0;
+                    uint32_t s = 0, deg = 0, u = 0;
                     uint64_t lab = INF64;
                     if (has) {
-                        uint32_t u = st.near_buf[i];
+                        u = st.near_buf[i];
                         atomicExch(&a.stamp_near[u], tag_cur);     // later improvements re-push u
                         __threadfence();
                         s = a.row_ptr[u];
                         deg = a.row_ptr[u + 1] - s;
                         lab = ldcg_u64(&a.label[u]);
                     }
+                    if (track) band_track(a, has, u, tag_band);
                     uint32_t incl = warp_inclusive_scan(deg);
                     uint32_t excl = incl - deg;
                     uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -394,7 +462,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                             labs[q] = __shfl_sync(FULL, lab, owner);
                             arc[q] = so + (j - eo);
                         }
-                        relax_group(a, st, t, valid, arc, labs, false, attempts, improved);
+                        relax_group(a, st, t, valid, arc, labs, false, wlo, whi, attempts,
+                                    improved);
                     }
                 }
             }
@@ -405,6 +474,11 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             break;
         }
         ++it;
+        const bool was_hp = hp;
+        if (hp) {
+            ++bands;               // later listings use a fresh tag
+            hp = false;
+        }
         if (it >= a.max_iters) {
             if (first) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
@@ -414,6 +488,14 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         uint32_t next = ldcg_u32(&ctl->near_count[ns]) + ldcg_u32(&ctl->heavy_count[ns]);
         if (next != 0) continue;
+        // Band drained: its heavy arcs first (one more iteration), then the
+        // split.  The band lists are cleared in the split, so no block can
+        // still be reading their counts here.
+        if (a.defer && !was_hp &&
+            (ldcg_u32(&ctl->band_count) | ldcg_u32(&ctl->band_hcount)) != 0) {
+            hp = true;
+            continue;
+        }
 
         // Near frontier drained: raise the threshold and split the far pile.
         // Every block has just read near_count[it % 3] to take this branch,
@@ -437,6 +519,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         if (first) {
             ctl->near_count[(its + 1) % 3] = 0;
             ctl->heavy_count[(its + 1) % 3] = 0;
+            ctl->band_count = 0;
+            ctl->band_hcount = 0;
         }
         stage_reset(st);
         PushTargets u;
@@ -466,9 +550,10 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
                 deg = r1 - r0;
             }
+            const bool cand = keep;
             if (keep) keep = atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
             push_near(a, st, u, to_near, v, deg);
-            push_far(a, st, u, keep, v, (uint32_t)d);
+            push_far(a, st, u, keep, cand, v, (uint32_t)d);
         }
         flush_stage(st, u, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
@@ -501,6 +586,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     if (first) {
         ctl->iterations = it;
         ctl->phases = phase;
+        ctl->bands = bands;
     }
 }
 // ---------------------------------------------------------------------------
@@ -580,6 +666,11 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.base_far = p.base_far;
     a.heavy_cap = g.heavy_chunk_cap;
     a.local_rounds = p.local_rounds;
+    a.stamp_band = ws.stamp_band;
+    a.band_q = ws.band_q;
+    a.band_hq = ws.band_hq;
+    a.base_band = p.base_band;
+    a.defer = p.delta <= g.max_w ? 1u : 0u;
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(geo.sssp_blocks),
                                        dim3(geo.threads), args, 0, s);

@@ -204,6 +204,29 @@ def test_result_is_independent_of_delta(delta, local):
     np.testing.assert_array_equal(res.edges, ref.edges)
 
 
+@pytest.mark.parametrize("delta,local", [(50, 0), (300, 8), (999, 0), (1000, 32)])
+def test_light_heavy_arc_split_on_grid_and_hubs(delta, local):
+    """With delta at or below the largest weight the bands relax light arcs
+    only and close with a heavy-arc pass; labels, preds and trees are
+    unchanged (a high-diameter grid, and an R-MAT graph whose hubs span
+    several heavy-row chunks)."""
+    for g, k in ((wl.grid(180, 140, 1000, seed=8), 40), (wl.rmat(12, 48, wmax=1000, seed=9), 25)):
+        pool = np.arange(g.n, dtype=np.int32) if g.n == 180 * 140 else wl.largest_cc(g)
+        seeds = wl.sample_distinct(pool, k, 8)
+        ref = oracle.steiner(g, seeds)
+        with st.SteinerGraph(g) as Gd:
+            Gd.set_param("delta", delta)
+            Gd.set_param("local_rounds", local)
+            rc, cell, dist, pred = Gd.voronoi(seeds)
+            res = Gd.query(seeds)
+        assert rc == st.STEINER_OK
+        np.testing.assert_array_equal(cell, ref.cell)
+        np.testing.assert_array_equal(dist, ref.dist)
+        np.testing.assert_array_equal(pred, ref.pred)
+        np.testing.assert_array_equal(res.edges, ref.edges)
+        assert res.total == ref.total
+
+
 def test_iteration_cap_reports_timeout():
     """A loop cap that cannot be met returns STEINER_ETIMEOUT (bounded
     device loops; no hang) and the handle stays usable."""
