@@ -40,7 +40,7 @@ struct ScanArgs {
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
                                          uint32_t arc, bool &overflow) {
     if (!valid) return;
-    uint2 e = __ldg(&a.adj[arc]);
+    uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
     uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[e.x]));
     if (lv == INF64 || lu == INF64) {
         // a reached vertex next to an unreached one: its true distance is

@@ -207,14 +207,16 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
 __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const PushTargets &t,
                                             const bool (&valid)[ILP], const uint32_t (&arc)[ILP],
                                             const uint64_t (&lab)[ILP], bool precheck,
-                                            uint32_t wlo, uint32_t whi,
+                                            bool stream, uint32_t wlo, uint32_t whi,
                                             unsigned long long &attempts,
                                             unsigned long long &improved) {
     uint2 e[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
         e[u] = make_uint2(0, 0);
-        if (valid[u]) e[u] = __ldg(&a.adj[arc[u]]);
+        // heavy-row chunks are streamed (evict first); short rows may be
+        // re-read by later hops and stay cacheable
+        if (valid[u]) e[u] = stream ? __ldcs(&a.adj[arc[u]]) : __ldg(&a.adj[arc[u]]);
     }
     uint64_t nd[ILP];
     bool imp[ILP];
@@ -377,7 +379,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         valid[q] = arc[q] < e;
                         labs[q] = lab;
                     }
-                    relax_group(a, st, t, valid, arc, labs, true, wlo, whi, attempts, improved);
+                    relax_group(a, st, t, valid, arc, labs, true, true, wlo, whi, attempts,
+                                improved);
                 }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
@@ -410,8 +413,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         labs[q] = __shfl_sync(FULL, lab, owner);
                         arc[q] = so + (j - eo);
                     }
-                    relax_group(a, st, t, valid, arc, labs, bsz == 32, wlo, whi, attempts,
-                                improved);
+                    relax_group(a, st, t, valid, arc, labs, bsz == 32, false, wlo, whi,
+                                attempts, improved);
                 }
             }
         }
@@ -462,8 +465,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                             labs[q] = __shfl_sync(FULL, lab, owner);
                             arc[q] = so + (j - eo);
                         }
-                        relax_group(a, st, t, valid, arc, labs, false, wlo, whi, attempts,
-                                    improved);
+                        relax_group(a, st, t, valid, arc, labs, false, false, wlo, whi,
+                                    attempts, improved);
                     }
                 }
             }
