@@ -429,6 +429,7 @@ def run_serve_mode(args, world, rank, local):
 
     G.query(qs[0])
     wall_sat, lat_sat = stream([0.0] * len(qs))
+    G_yield_div = G.get_param("batch_yield_div")
     qps = len(qs) / wall_sat
     arrivals = wl.poisson_arrivals(len(qs), 0.7 * qps, 0x5EED + 5)
     wall_p, lat_p = stream(arrivals)
@@ -445,7 +446,8 @@ def run_serve_mode(args, world, rank, local):
             "ms_per_step": 1e3 * wall_sat, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "rmat24_serve", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
-                       "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64},
+                       "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64,
+                       "yield_div": G_yield_div},
             "saturated": {"p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
                           "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},
             "poisson_0p7": {"rate_qps": 0.7 * qps, "achieved_qps": len(qs) / wall_p,

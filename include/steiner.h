@@ -191,6 +191,10 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  (0 = off): a block keeps relaxing the vertices it just
  *                  queued, a hop per round, before the grid barrier
  *   "batch_delta"  band width of the multi-query engine (0 = "delta")
+ *   "batch_yield_div"  a serving launch returns to the host (to retire and
+ *                  admit) once 1/batch_yield_div of its in-flight queries
+ *                  converged (1..64, default 1: whole waves), or earlier
+ *                  when a request waits and a slot is free
  *   "max_iters"    frontier iteration cap (STEINER_ETIMEOUT beyond it)
  * steiner_get_param also reads "sssp_max_blocks", "sm_count",
  * "heavy_chunks" and the multi-query engine's tracing counters

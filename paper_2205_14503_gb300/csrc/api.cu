@@ -479,9 +479,8 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     if (!strcmp(key, "delta")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "delta out of range");
         G->delta = (uint32_t)value;
-    } else if (!strcmp(key, "batch_delta")) {
-        if (value < 0 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "batch_delta out of range");
-        return batch_set_delta(G, (uint32_t)value);
+    } else if (!strncmp(key, "batch_", 6)) {
+        return batch_set_param(G, key, value);
     } else if (!strcmp(key, "sssp_blocks")) {
         // persistent grid size: 1 .. all co-resident blocks (0 = all)
         int maxb = G->geo.sssp_max_blocks;

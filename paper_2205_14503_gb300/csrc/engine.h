@@ -28,7 +28,7 @@ const Geometry &api_geometry(steiner_graph *G);
 void api_set_error(const std::string &msg);
 void destroy_batch(BatchEngine *b);
 int64_t batch_counter(BatchEngine *B, const char *key);
-int batch_set_delta(steiner_graph *G, uint32_t d);
+int batch_set_param(steiner_graph *G, const char *key, int64_t value);
 int api_run_tail(steiner_graph *G, uint64_t *pairtab, uint32_t *pred_base, uint32_t pred_stride,
                  uint32_t k, bool overflow, steiner_result_t *out);
 int api_sorted_seeds(steiner_graph *G, const int32_t *seeds, uint32_t k, std::vector<int32_t> &out);

@@ -60,6 +60,13 @@ struct BatchEngine {
     // Band width of every slot's near/far threshold (0 = the graph's
     // single-query default).
     uint32_t batch_delta = 0;
+    // A yielding launch returns once popc(in flight) / yield_div slots
+    // converged (at least one), or when the doorbell rings (a request waits
+    // and a slot is free).  1 (the default) retires whole waves: slots that
+    // started together keep their frontiers aligned, so one CSR row visit
+    // serves many slots and one retirement scan covers many queries;
+    // larger divisors retire earlier, in smaller groups.
+    uint32_t yield_div = 1;
     // cumulative wall time (ms) and counters, for tracing
     double ms_sssp = 0, ms_scan = 0, ms_tail = 0, ms_admit = 0;
     uint64_t launches = 0, relax_attempts = 0, iterations_run = 0;
@@ -84,7 +91,6 @@ struct BatchEngine {
         int per_sm = mq_occupancy(256);
         int sms = api_geometry(G).sm_count;
         blocks = std::max(1, per_sm) * sms;
-        delta = batch_delta ? batch_delta : api_delta(G);
         fixed = (uint64_t)g.n * MQ_SLOTS * 12;
         ready = true;
         return STEINER_OK;
@@ -100,6 +106,8 @@ struct BatchEngine {
         h_masks = nullptr;
         ready = false;
     }
+
+    uint32_t cur_delta() const { return batch_delta ? batch_delta : api_delta(G); }
 
     int free_slot() const {
         for (int q = 0; q < MQ_SLOTS; ++q)
@@ -132,7 +140,7 @@ struct BatchEngine {
         cudaError_t e = mq_launch_clear(api_graph(G), m, staged, s);
         for (unsigned long long mm = staged; mm && e == cudaSuccess; mm &= mm - 1) {
             int q = __builtin_ctzll(mm);
-            e = mq_launch_seed(api_graph(G), m, q, slots[q].k, delta, s);
+            e = mq_launch_seed(api_graph(G), m, q, slots[q].k, cur_delta(), s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         unsigned long long done = staged;
@@ -204,12 +212,13 @@ struct BatchEngine {
         ++launches;
         h_masks[0] = inflight;
         h_masks[1] = 0;
+        delta = cur_delta();
         cudaError_t e = cudaMemcpyAsync(&m.ctl->inflight, &h_masks[0], 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&m.ctl->converged, &h_masks[1], 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = mq_launch_sssp(api_graph(G), m, blocks, delta, 1u << 20,
-                               yield ? std::max(1, __builtin_popcountll(inflight) / 8) : 0,
+                               yield ? std::max(1u, (uint32_t)__builtin_popcountll(inflight) / yield_div) : 0u,
                                doorbell_dev, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_ctl, m.ctl, sizeof(MqControl), cudaMemcpyDeviceToHost, s);
@@ -309,7 +318,6 @@ void destroy_batch(BatchEngine *b) {
 // "batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit",
 // "batch_launches", "batch_iterations", "batch_relax_attempts"; "batch_reset"
 // clears them).
-int batch_set_delta(steiner_graph *G, uint32_t d);
 
 int64_t batch_counter(BatchEngine *B, const char *key) {
     if (!B) return -1;
@@ -321,7 +329,8 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_launches") return (int64_t)B->launches;
     if (k == "batch_iterations") return (int64_t)B->iterations_run;
     if (k == "batch_relax_attempts") return (int64_t)B->relax_attempts;
-    if (k == "batch_delta") return B->delta;
+    if (k == "batch_delta") return B->cur_delta();
+    if (k == "batch_yield_div") return B->yield_div;
     if (k.rfind("batch_t", 0) == 0 && k.size() == 8 && B->h_ctl) return (int64_t)B->h_ctl->t_part[k[7] - '0'];
     if (k == "batch_items" && B->h_ctl) return (int64_t)B->h_ctl->items_total;
     if (k == "batch_pairs" && B->h_ctl) return (int64_t)B->h_ctl->pairs_total;
@@ -342,11 +351,28 @@ static BatchEngine *engine_of(steiner_graph *G) {
     return B;
 }
 
-int batch_set_delta(steiner_graph *G, uint32_t d) {
+// Engine settings (steiner_set_param keys "batch_delta", "batch_yield_div").
+int batch_set_param(steiner_graph *G, const char *key, int64_t value) {
     BatchEngine *B = engine_of(G);
-    B->batch_delta = d;
-    if (B->ready) B->delta = d ? d : api_delta(G);
-    return STEINER_OK;
+    std::string k(key);
+    if (k == "batch_delta") {
+        if (value < 0 || value > 0x7FFFFFFF) {
+            api_set_error("batch_delta out of range");
+            return STEINER_EINVAL;
+        }
+        B->batch_delta = (uint32_t)value;
+        return STEINER_OK;
+    }
+    if (k == "batch_yield_div") {
+        if (value < 1 || value > MQ_SLOTS) {
+            api_set_error("batch_yield_div out of range (1..64)");
+            return STEINER_EINVAL;
+        }
+        B->yield_div = (uint32_t)value;
+        return STEINER_OK;
+    }
+    api_set_error(std::string("unknown parameter ") + key);
+    return STEINER_EINVAL;
 }
 
 // ---------------------------------------------------------------------------
