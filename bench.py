@@ -458,6 +458,57 @@ def run_serve_mode(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation_mode(args, world, rank, local):
+    """Relaxation order (the paper's priority-ordered messages against a
+    plain frontier): per single-query workload, the Voronoi phase as a
+    Bellman-Ford frontier (one unbounded band), as near/far bands at the
+    tuned width, and with the tuned block-local rounds; time, relaxations
+    per arc and iterations of each."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import autotune
+    from paper_2205_14503_gb300 import steiner as st
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    cfgs = [1, 2, 4] + ([3] if args.with_large else [])
+    rows = []
+    for cfg in cfgs:
+        g = wl.config_graph(cfg)
+        seeds = wl.config_seed_sets(cfg, g)[0]
+        with st.SteinerGraph(g, device=local) as G:
+            tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
+            variants = [("frontier (Bellman-Ford)", 0x7FFFFFFF, 0),
+                        ("near/far", tuned["delta"], 0),
+                        ("near/far + block-local rounds", tuned["delta"], tuned["local_rounds"])]
+            ref = None
+            for name, delta, lr in variants:
+                if name.endswith("rounds") and lr == 0:
+                    continue
+                G.set_param("delta", delta)
+                G.set_param("local_rounds", lr)
+                G.query_detail(seeds, pairs=False)
+                ms, att, its = [], [], []
+                for _ in range(max(1, args.steps)):
+                    r = G.query_detail(seeds, pairs=False)
+                    ms.append(r.stats["ms_voronoi"])
+                    att.append(r.stats["relax_attempts"])
+                    its.append(r.stats["iterations"])
+                if ref is None:
+                    ref = r.total
+                assert r.total == ref, "schedules must reach the same tree"
+                rows.append({"workload": g.name, "order": name, "delta": delta, "local_rounds": lr,
+                             "ms_voronoi": statistics.median(ms),
+                             "relaxations_per_arc": statistics.mean(att) / g.n_arcs,
+                             "iterations": statistics.mean(its), "total": int(r.total)})
+        del g
+    print(json.dumps({"metric": "Voronoi relaxation-order ablation", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,9 +523,12 @@ def main():
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve"], default="plain",
+    ap.add_argument("--with-large", action="store_true",
+                    help="ablation mode: include the R-MAT scale-26 workload")
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation"], default="plain",
                     help="plain: the grid single-query workload (default); batch: R-MAT 22 with "
-                         "64 batched queries; serve: R-MAT 24 query stream")
+                         "64 batched queries; serve: R-MAT 24 query stream; ablation: "
+                         "relaxation order on the single-query workloads")
     ap.add_argument("--queries", type=int, default=2000, help="serve mode: stream length")
     ap.add_argument("--plain-sample", type=int, default=200,
                     help="serve mode: queries timed one at a time for the plain comparison")
@@ -487,6 +541,8 @@ def main():
             run_batch_mode(args, world, rank, local)
         elif args.mode == "serve":
             run_serve_mode(args, world, rank, local)
+        elif args.mode == "ablation":
+            run_ablation_mode(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:
