@@ -40,7 +40,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = 2            # the 4096^2 grid, 256 seeds
-PROFILE = os.path.join(ROOT, "profiles", "sssp_grid4096_k256.md")
 SSSP_SOURCES = ["paper_2205_14503_gb300/csrc/voronoi.cu", "paper_2205_14503_gb300/csrc/common.cuh",
                 "paper_2205_14503_gb300/csrc/internal.h"]
 
@@ -53,11 +52,11 @@ def sssp_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per SSSP launch from the committed ncu summary, or None
-    if the summary is absent or the kernel source changed since."""
+def profiled_traffic(workload_name: str):
+    """DRAM bytes per SSSP launch from the committed ncu summary of this
+    workload, or None if it is absent or the kernel source changed since."""
     try:
-        text = open(PROFILE).read()
+        text = open(os.path.join(ROOT, "profiles", f"sssp_{workload_name}.md")).read()
     except OSError:
         return None
     m1 = re.search(r"sssp_source_hash:\s*([0-9a-f]+)", text)
@@ -152,20 +151,21 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def workload(rank: int, side: int | None = None, k: int | None = None):
+def workload(rank: int, side: int | None = None, k: int | None = None, cfg: int = WORKLOAD):
     """The benchmark graph and seed set.  ``side``/``k`` shrink the grid for
-    profiling captures (same seed density); the default is the workload."""
+    profiling captures (same seed density); ``cfg`` picks another
+    single-query workload (1 R-MAT 16, 3 R-MAT 26); the default is the grid."""
     import paper_2205_14503_gb300.workloads as wl
     if side:
         g = wl.grid(side, side, 1000, wl.CONFIG_SEED + WORKLOAD)
         seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), k or 64,
                                    (wl.CONFIG_SEED + WORKLOAD) ^ 0x51ED)
     else:
-        g = wl.config_graph(WORKLOAD)
-        (seeds,) = wl.config_seed_sets(WORKLOAD, g)
+        g = wl.config_graph(cfg)
+        seeds = wl.config_seed_sets(cfg, g)[0]
     if rank > 0:    # replicas run their own queries of the same size
-        seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), seeds.size,
-                                   0x5EED + WORKLOAD + 1000 * rank)
+        pool = np.arange(g.n, dtype=np.int32) if side or cfg == WORKLOAD else wl.largest_cc(g)
+        seeds = wl.sample_distinct(pool, seeds.size, 0x5EED + cfg + 1000 * rank)
     return g, seeds
 
 
@@ -183,10 +183,17 @@ def cpu_oracle_time(g, seeds, budget_s: float = 30.0):
     return r, times
 
 
-def config_dict(g, seeds):
-    side = int(round(g.n ** 0.5))
-    return {"workload": f"grid{side}_k{seeds.size}",
-            "graph": f"{side}x{side} 4-connected grid, w~U[1,1000]",
+def config_dict(g, seeds, cfg: int = WORKLOAD, side: int | None = None):
+    import paper_2205_14503_gb300.workloads as wl
+    if side or cfg == WORKLOAD:
+        s = int(round(g.n ** 0.5))
+        name, desc = f"grid{s}_k{seeds.size}", f"{s}x{s} 4-connected grid, w~U[1,1000]"
+    else:
+        c = wl.CONFIGS[cfg]
+        name = c["name"]
+        desc = (f"R-MAT scale {c['scale']}, edge factor 16, (a,b,c)=(.57,.19,.19), "
+                f"w~U[1,{c['wmax']}]")
+    return {"workload": name, "graph": desc,
             "n": int(g.n), "arcs": int(g.n_arcs), "k": int(seeds.size),
             "l2": f"inputs larger than L2 (adjacency {g.n_arcs * 8 >> 20} MiB, "
                   f"labels {g.n * 8 >> 20} MiB)"}
@@ -198,7 +205,7 @@ METRIC = "Steiner trees/s (Voronoi SSSP + bridge scan + MST + expansion)"
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    g, seeds = workload(0, args.side, args.k)
+    g, seeds = workload(0, args.side, args.k, args.workload)
     import oracle
     for _ in range(args.warmup):
         oracle.steiner(g, seeds, want_labels=False)
@@ -213,7 +220,7 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_dict(g, seeds),
+            "config": config_dict(g, seeds, args.workload, args.side),
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "trees/s", "cores": 1,
                              "sample": "whole queries of the workload, single-threaded C oracle"},
             "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0,
@@ -230,7 +237,7 @@ def run_ours(args, world, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)
-    g, seeds = workload(rank, args.side, args.k)
+    g, seeds = workload(rank, args.side, args.k, args.workload)
     t0 = time.perf_counter()
     G = st.SteinerGraph(g, device=local)
     load_s = time.perf_counter() - t0
@@ -293,13 +300,14 @@ def run_ours(args, world, rank, local):
     alg_bytes = 16 * m_arcs + 12 * n          # per SSSP launch (one query)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (sssp_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    cfgd = config_dict(g, seeds, args.workload, args.side)
+    traffic = profiled_traffic(cfgd["workload"])
     line = {
         "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_dict(g, seeds),
+        "config": cfgd,
         "roofline": {"kernel": "sssp_kernel (Voronoi near/far SSSP)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
@@ -537,6 +545,9 @@ def main():
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3],
+                    help="plain mode: single-query workload (2 = the 4096^2 grid, the default; "
+                         "1 = R-MAT 16, 3 = R-MAT 26, use with --no-cpu-baseline)")
     ap.add_argument("--with-large", action="store_true",
                     help="ablation mode: include the R-MAT scale-26 workload")
     ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation"], default="plain",
