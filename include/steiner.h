@@ -109,7 +109,13 @@ typedef struct {
  *   col      host, n_arcs neighbour ids
  *   w        host, n_arcs weights
  * On success *out receives a handle; the caller keeps ownership of the
- * arrays.  Errors: STEINER_EINVAL (malformed graph or n_arcs >= 2^32),
+ * arrays.  On a skewed degree distribution the device copy numbers the
+ * vertices by descending degree (ties by id) for cache locality; every
+ * result (tree edges, pair arcs, cell/dist/pred) is still in the caller's
+ * vertex ids and arc indices, and the tie rules use the caller's order.
+ * The environment variable STEINER_RELABEL=0 or 1, read here, forces this
+ * internal order off or on.
+ * Errors: STEINER_EINVAL (malformed graph or n_arcs >= 2^32),
  * STEINER_ENOMEM, STEINER_ECUDA.  Cites: Table "preliminaries_notation"
  * (positive integer distances); Section "Evaluation" (symmetric arcs).
  */

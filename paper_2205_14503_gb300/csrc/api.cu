@@ -370,11 +370,42 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     if ((e = cudaMallocHost((void **)&G->h_ctl, sizeof(Control))) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMallocHost"));
-    // heavy rows, listed in CHUNK-arc pieces
+    // Internal vertex order: on a skewed degree distribution, descending
+    // degree (ties by caller id), so the hubs' labels, which most arcs
+    // point to, share L2 sectors.  STEINER_RELABEL=0/1 forces it off/on.
+    uint32_t max_deg = 0;
+    for (uint32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, row_ptr[v + 1] - row_ptr[v]);
+    const double avg_deg = n_arcs ? (double)n_arcs / n : 0.0;
+    bool relabel = n_arcs > 0 && n >= 1024 && max_deg >= 16.0 * std::max(1.0, avg_deg);
+    if (const char *env = getenv("STEINER_RELABEL")) relabel = n_arcs > 0 && atoi(env) != 0;
+    std::vector<uint32_t> h_orig_of, h_new_of, h_new_rp;
+    if (relabel) {
+        std::vector<uint64_t> start((size_t)max_deg + 1, 0);
+        for (uint32_t v = 0; v < n; ++v) ++start[row_ptr[v + 1] - row_ptr[v]];
+        uint64_t pos = 0;
+        for (int64_t d = max_deg; d >= 0; --d) {
+            uint64_t c = start[d];
+            start[d] = pos;
+            pos += c;
+        }
+        h_orig_of.resize(n);
+        h_new_of.resize(n);
+        for (uint32_t v = 0; v < n; ++v) {
+            uint32_t u = (uint32_t)start[row_ptr[v + 1] - row_ptr[v]]++;
+            h_orig_of[u] = v;
+            h_new_of[v] = u;
+        }
+        h_new_rp.resize((size_t)n + 1);
+        h_new_rp[0] = 0;
+        for (uint32_t u = 0; u < n; ++u)
+            h_new_rp[u + 1] = h_new_rp[u] + (row_ptr[h_orig_of[u] + 1] - row_ptr[h_orig_of[u]]);
+    }
+    const uint32_t *irp = relabel ? h_new_rp.data() : row_ptr;     // internal row offsets
+    // heavy rows, listed in CHUNK-arc pieces (internal ids)
     std::vector<uint64_t> chunks;
     uint64_t cap = 0;
     for (uint32_t v = 0; v < n; ++v) {
-        uint32_t deg = row_ptr[v + 1] - row_ptr[v];
+        uint32_t deg = irp[v + 1] - irp[v];
         if (deg >= HEAVY_DEG) {
             uint32_t nc = (deg + CHUNK - 1) / CHUNK;
             for (uint32_t c = 0; c < nc; ++c) chunks.push_back(((uint64_t)v << 32) | c);
@@ -386,6 +417,11 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
     if ((e = dalloc(G->g.row_ptr, (uint64_t)n + 1)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     if ((e = dalloc(G->g.adj, n_arcs)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     if ((e = dalloc(G->g.heavy_chunks, chunks.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if (relabel) {
+        if ((e = dalloc(G->g.orig_row_ptr, (uint64_t)n + 1)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+        if ((e = dalloc(G->g.orig_of, n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+        if ((e = dalloc(G->g.new_of, n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    }
     int32_t *d_col = nullptr;
     uint32_t *d_w = nullptr, *d_bad = nullptr;
     if ((e = dalloc(d_col, n_arcs)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
@@ -400,7 +436,13 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
     }
     cudaStream_t s = G->stream;
     uint32_t bad[2] = {0, 0};     // flags, largest weight
-    e = cudaMemcpyAsync(G->g.row_ptr, row_ptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(G->g.row_ptr, irp, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && relabel)
+        e = cudaMemcpyAsync(G->g.orig_row_ptr, row_ptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && relabel)
+        e = cudaMemcpyAsync(G->g.orig_of, h_orig_of.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && relabel)
+        e = cudaMemcpyAsync(G->g.new_of, h_new_of.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_arcs)
         e = cudaMemcpyAsync(d_col, col, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_arcs)
@@ -410,7 +452,9 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 8, s);
     if (e == cudaSuccess)
-        e = launch_validate_graph(G->g.row_ptr, d_col, d_w, n, n_arcs, G->g.adj, d_bad, d_bad + 1, s);
+        e = launch_validate_graph(relabel ? G->g.orig_row_ptr : G->g.row_ptr, d_col, d_w, n, n_arcs,
+                                  G->g.adj, G->g.new_of, relabel ? G->g.row_ptr : nullptr, d_bad,
+                                  d_bad + 1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bad, d_bad, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_col);
@@ -440,7 +484,6 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
         for (uint64_t i = 0; i < n_arcs; i += step, ++cnt) avg_w += w[i];
         avg_w /= (double)cnt;
     }
-    double avg_deg = n_arcs ? (double)n_arcs / n : 1.0;
     double d = 32.0 * std::max(1.0, avg_w) / std::max(1.0, avg_deg);
     G->delta = (uint32_t)std::min(std::max(d, 1.0), 1.0e9);
     if (const char *env = getenv("STEINER_DELTA")) G->delta = (uint32_t)std::max(1L, atol(env));
@@ -463,7 +506,7 @@ void steiner_free_graph(steiner_graph_t G) {
                     ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
                     ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
                     ws.best, ws.tree_key, ws.tree_key2, ws.tree_w, ws.tree_w2, G->g.row_ptr,
-                    G->g.adj, G->g.heavy_chunks};
+                    G->g.adj, G->g.heavy_chunks, G->g.orig_row_ptr, G->g.orig_of, G->g.new_of};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (auto &ev : G->ev)

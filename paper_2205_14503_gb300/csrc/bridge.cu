@@ -35,10 +35,15 @@ struct ScanArgs {
     uint32_t k;
     bool pairs;
     uint32_t *err;
+    const uint32_t *orig_of;         // internal -> caller ids (null: identity)
+    const uint32_t *orig_row_ptr;
 };
 
+// Arc `arc` of row v (which starts at rs).  The bridge key carries the
+// caller's arc index, so ties between equal bridges break on the caller's
+// CSR order whatever the internal vertex order.
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
-                                         uint32_t arc, bool &overflow) {
+                                         uint32_t rs, uint32_t arc, bool &overflow) {
     if (!valid) return;
     uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
     uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[e.x]));
@@ -58,7 +63,7 @@ __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t
             overflow = true;
             return;
         }
-        uint64_t key = (b << 32) | arc;
+        uint64_t key = (b << 32) | caller_arc(a.orig_of, a.orig_row_ptr, v, rs, arc);
         uint64_t *slot = &a.pairtab[pair_slot(cv, cu, a.k)];
         if (key < ldcg_u64(slot))
             atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
@@ -76,10 +81,12 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
         if (wi < a.n_heavy_chunks) {
             uint64_t item = a.heavy_chunks[wi];
             uint32_t v = (uint32_t)(item >> 32), c = (uint32_t)item;
-            uint32_t s = a.row_ptr[v] + c * CHUNK;
+            uint32_t rs = a.row_ptr[v];
+            uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
             uint64_t lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
-            for (uint32_t b = s; b < e; b += 32) scan_arc(a, b + lane < e, v, lv, b + lane, overflow);
+            for (uint32_t b = s; b < e; b += 32)
+                scan_arc(a, b + lane < e, v, lv, rs, b + lane, overflow);
         } else {
             uint32_t v = (wi - a.n_heavy_chunks) * 32 + lane;
             uint32_t s = 0, deg = 0;
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
                 uint32_t eo = __shfl_sync(FULL, excl, owner);
                 uint64_t lo = __shfl_sync(FULL, lv, owner);
                 uint32_t vo = (wi - a.n_heavy_chunks) * 32 + owner;
-                scan_arc(a, valid, vo, lo, so + (j - eo), overflow);
+                scan_arc(a, valid, vo, lo, so, so + (j - eo), overflow);
             }
         }
     }
@@ -236,6 +243,8 @@ cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs
     a.k = k;
     a.pairs = pairs && k > 1;
     a.err = &ws.ctl->err;
+    a.orig_of = g.orig_of;
+    a.orig_row_ptr = g.orig_row_ptr;
     if (a.pairs) {
         uint64_t slots = (uint64_t)k * (k - 1) / 2;
         cudaError_t e = cudaMemsetAsync(ws.pairtab, 0xFF, slots * sizeof(uint64_t), s);

@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
                                                        const int32_t *__restrict__ col,
                                                        const uint32_t *__restrict__ w,
                                                        uint32_t n, uint2 *__restrict__ adj,
+                                                       const uint32_t *__restrict__ new_of,
+                                                       const uint32_t *__restrict__ new_row_ptr,
                                                        uint32_t *bad, uint32_t *max_w) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -57,12 +59,15 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
             uint32_t e = so + (j - eo);
             int32_t c = col[e];
             uint32_t wt = w[e];
-            adj[e] = make_uint2((uint32_t)c, wt);
             wmax = max(wmax, wt);
             if (c < 0 || (uint32_t)c >= n) {
                 flags |= BAD_RANGE;
                 continue;
             }
+            if (new_of)
+                adj[new_row_ptr[new_of[src]] + (e - so)] = make_uint2(new_of[c], wt);
+            else
+                adj[e] = make_uint2((uint32_t)c, wt);
             if ((uint32_t)c == src) flags |= BAD_SELF;
             if (wt == 0) flags |= BAD_WEIGHT;
             if (e > so && col[e - 1] >= c) flags |= BAD_ORDER;
@@ -75,13 +80,15 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
 }
 
 cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,
-                                  uint32_t n, uint64_t m, uint2 *adj, uint32_t *bad,
-                                  uint32_t *max_w, cudaStream_t s) {
+                                  uint32_t n, uint64_t m, uint2 *adj, const uint32_t *new_of,
+                                  const uint32_t *new_row_ptr, uint32_t *bad, uint32_t *max_w,
+                                  cudaStream_t s) {
     (void)m;
     uint64_t blocks = ((uint64_t)n + 255) / 256;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
     if (blocks < 1) blocks = 1;
-    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, bad, max_w);
+    validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, new_of, new_row_ptr,
+                                                      bad, max_w);
     return cudaGetLastError();
 }
 

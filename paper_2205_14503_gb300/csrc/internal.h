@@ -24,7 +24,29 @@ struct DevGraph {
     uint32_t n_heavy_chunks = 0;
     uint32_t heavy_chunk_cap = 0;   // bound on chunk entries a frontier can hold
     uint32_t max_w = 0;             // largest arc weight
+    // Internal vertex order.  On a skewed degree distribution the vertices
+    // are renumbered by descending degree (ties by id), so the labels of
+    // the hubs that most arcs point to share L2 sectors; rows keep the
+    // caller's order of neighbours (ascending caller id).  All results are
+    // reported in the caller's ids and arc indices.  Null: identity.
+    uint32_t *orig_of = nullptr;     // internal id -> caller id, n
+    uint32_t *new_of = nullptr;      // caller id -> internal id, n
+    uint32_t *orig_row_ptr = nullptr;   // the caller's row offsets, n + 1
 };
+
+// Caller's arc index of internal arc `arc` of internal row v starting at rs.
+__device__ __forceinline__ uint32_t caller_arc(const uint32_t *orig_of, const uint32_t *orig_row_ptr,
+                                               uint32_t v, uint32_t rs, uint32_t arc) {
+    return orig_of ? orig_row_ptr[orig_of[v]] + (arc - rs) : arc;
+}
+
+__device__ __forceinline__ uint32_t caller_id(const uint32_t *orig_of, uint32_t v) {
+    return orig_of ? orig_of[v] : v;
+}
+
+__device__ __forceinline__ uint32_t internal_id(const uint32_t *new_of, uint32_t v) {
+    return new_of ? new_of[v] : v;
+}
 
 constexpr int TRACE_LEN = 64;
 
@@ -134,8 +156,13 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
 int mst_occupancy(int threads);
 
 // graph.cu
+// Validates the caller's CSR (row_ptr, col, w) and writes the interleaved
+// internal adjacency: arc e of caller row u goes to
+// new_row_ptr[new_of[u]] + (e - row_ptr[u]) with neighbour new_of[col[e]]
+// (new_of / new_row_ptr null: the identity).
 cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col,
                                   const uint32_t *w, uint32_t n, uint64_t m, uint2 *adj,
+                                  const uint32_t *new_of, const uint32_t *new_row_ptr,
                                   uint32_t *bad, uint32_t *max_w, cudaStream_t s);
 
 }  // namespace stn

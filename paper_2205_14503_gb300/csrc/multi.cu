@@ -546,7 +546,8 @@ __global__ void mq_clear_rows_kernel(uint32_t n, uint64_t *label, uint32_t *pred
 }
 
 __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n, const int32_t *seeds,
-                               uint32_t k, uint32_t q, uint32_t delta, MqState m) {
+                               const uint32_t *__restrict__ new_of, uint32_t k, uint32_t q,
+                               uint32_t delta, MqState m) {
     MqControl *ctl = m.ctl;
     uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t it = ctl->it;
@@ -560,7 +561,7 @@ __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n,
         ctl->slot_overflow &= ~bit;
     }
     if (r >= k) return;
-    uint32_t s = (uint32_t)seeds[r];
+    uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
     m.label[(uint64_t)s * MQ_SLOTS + q] = (uint64_t)r;
     m.pred[(uint64_t)s * MQ_SLOTS + q] = SEED_ARC;
     atomicOr(&m.nmask[s], bit);
@@ -590,10 +591,14 @@ struct MqScanArgs {
     const uint32_t *k;
     unsigned long long slots;
     MqControl *ctl;
+    const uint32_t *orig_of;         // internal -> caller ids (null: identity)
+    const uint32_t *orig_row_ptr;
 };
 
+// Arc `arc` of row v (which starts at rs) for slot q; bridge keys carry the
+// caller's arc index, as in the single-query scan.
 __device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, uint32_t v,
-                                             uint32_t arc, uint32_t q,
+                                             uint32_t rs, uint32_t arc, uint32_t q,
                                              unsigned long long &overflow) {
     if (!valid) return;
     uint2 e = __ldg(&a.adj[arc]);
@@ -613,7 +618,7 @@ __device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, ui
             overflow |= 1ull << q;
             return;
         }
-        uint64_t key = (b << 32) | arc;
+        uint64_t key = (b << 32) | caller_arc(a.orig_of, a.orig_row_ptr, v, rs, arc);
         uint64_t *slot = &a.pairtab[q][pair_slot(cv, cu, a.k[q])];
         if (key < ldcg_u64(slot))
             atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
@@ -623,8 +628,8 @@ __device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, ui
 // One vertex's arcs [s0, s1) for every slot of the launch.  Lanes are
 // grouped as in the SSSP kernel: a group of g lanes takes one arc, lane t of
 // the group the t-th slot (t + 32 on a second pass when over 32 slots).
-__device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uint32_t s0,
-                                            uint32_t s1, uint32_t cnt, uint32_t gsh,
+__device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uint32_t rs,
+                                            uint32_t s0, uint32_t s1, uint32_t cnt, uint32_t gsh,
                                             unsigned long long &overflow) {
     const uint32_t lane = lane_id();
     const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh, tl = lane & (g - 1);
@@ -636,7 +641,7 @@ __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uin
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 uint32_t arc = j0 + k * apr + grp;
-                mq_scan_pair(a, has_slot && arc < s1, v, arc, q, overflow);
+                mq_scan_pair(a, has_slot && arc < s1, v, rs, arc, q, overflow);
             }
         }
     }
@@ -655,9 +660,10 @@ __global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
         if (wi < a.n_heavy_chunks) {
             uint64_t item = a.heavy_chunks[wi];
             uint32_t v = (uint32_t)(item >> 32), c = (uint32_t)item;
-            uint32_t s = a.row_ptr[v] + c * CHUNK;
+            uint32_t rs = a.row_ptr[v];
+            uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
-            mq_scan_row(a, v, s, e, cnt, gsh, overflow);
+            mq_scan_row(a, v, rs, s, e, cnt, gsh, overflow);
         } else {
             uint32_t v0 = (wi - a.n_heavy_chunks) * 32;
             uint32_t vl = v0 + lane;
@@ -666,7 +672,7 @@ __global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
             for (uint32_t l = 0; l < 32 && v0 + l < a.n; ++l) {
                 uint32_t s = __shfl_sync(FULL, rs, l), e = __shfl_sync(FULL, re, l);
                 if (e - s >= HEAVY_DEG) continue;          // covered by the chunk list
-                mq_scan_row(a, v0 + l, s, e, cnt, gsh, overflow);
+                mq_scan_row(a, v0 + l, s, s, e, cnt, gsh, overflow);
             }
         }
     }
@@ -753,7 +759,7 @@ cudaError_t mq_launch_clear(const DevGraph &g, MqState &m, unsigned long long ma
 
 cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uint32_t delta,
                            cudaStream_t s) {
-    mq_seed_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, g.n, m.seeds[q], k, (uint32_t)q,
+    mq_seed_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, g.n, m.seeds[q], g.new_of, k, (uint32_t)q,
                                                     delta, m);
     return cudaGetLastError();
 }
@@ -806,6 +812,8 @@ cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slo
     a.k = m.d_k;
     a.slots = slots;
     a.ctl = m.ctl;
+    a.orig_of = g.orig_of;
+    a.orig_row_ptr = g.orig_row_ptr;
     uint64_t work = (uint64_t)g.n_heavy_chunks + (g.n + 31) / 32;
     uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + 7) / 8, 152ull * 32));
     mq_scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);

@@ -131,6 +131,9 @@ __device__ __forceinline__ void emit_edge(uint32_t a, uint32_t b, uint32_t w, ui
 // and the pred load are issued together, so a hop costs two dependent loads
 // (pred arc, then the arc's record) instead of three.
 __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
+                              const uint32_t *__restrict__ orig_of,
+                              const uint32_t *__restrict__ new_of,
+                              const uint32_t *__restrict__ orig_row_ptr,
                               uint32_t n, const uint32_t *__restrict__ e_arc,
                               const uint32_t *__restrict__ e_mst,
                               const uint32_t *__restrict__ pred_arc, uint32_t pred_stride,
@@ -140,13 +143,25 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * E; t += gridDim.x * blockDim.x) {
         const uint32_t j = t >> 1, side = t & 1;
         if (!e_mst[j]) continue;
-        uint32_t arc = e_arc[j];
+        // the pair table holds the caller's arc index: its tail in the
+        // caller's CSR, then the same arc in the internal order
+        const uint32_t carc = e_arc[j];
+        uint32_t tail, arc;
+        if (orig_of) {
+            const uint32_t ct = arc_owner(orig_row_ptr, n, carc);
+            tail = new_of[ct];
+            arc = row_ptr[tail] + (carc - orig_row_ptr[ct]);
+        } else {
+            tail = arc_owner(row_ptr, n, carc);
+            arc = carc;
+        }
         uint2 e = adj[arc];
         uint32_t x = e.x;
         if (side == 0) {
             atomicAdd(&ctl->n_mst, 1u);
-            x = arc_owner(row_ptr, n, arc);
-            emit_edge(x, e.x, e.y, nbits, key, wout, cap, ctl);
+            x = tail;
+            emit_edge(caller_id(orig_of, x), caller_id(orig_of, e.x), e.y, nbits, key, wout, cap,
+                      ctl);
         }
         for (uint32_t steps = 0; steps < n; ++steps) {
             uint32_t pa = pred_arc[(uint64_t)x * pred_stride];
@@ -154,7 +169,8 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
             uint32_t old = atomicExch(&mark[x], tag);
             uint2 pe = adj[pa];              // independent of the exchange's result
             if (old == tag) break;           // the rest of the chain is another walker's
-            emit_edge(x, pe.x, pe.y, nbits, key, wout, cap, ctl);
+            emit_edge(caller_id(orig_of, x), caller_id(orig_of, pe.x), pe.y, nbits, key, wout, cap,
+                      ctl);
             x = pe.x;
         }
     }
@@ -318,7 +334,8 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
     if (k < 2) return cudaSuccess;
     uint64_t slots = (uint64_t)k * (k - 1) / 2;
     uint32_t blocks = (uint32_t)std::min<uint64_t>((2 * slots + 255) / 256, 152ull * 8);
-    expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
+    expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.orig_of, g.new_of, g.orig_row_ptr,
+                                         g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
                                          ws.pred_stride, ws.mark, tag, n_bits, ws.tree_key,
                                          ws.tree_w, ws.tree_cap, ws.ctl);
     cudaError_t e = cudaGetLastError();

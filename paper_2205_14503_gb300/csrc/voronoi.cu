@@ -67,6 +67,7 @@ __global__ void init_labels_kernel(uint32_t n, uint64_t *__restrict__ label,
 }
 
 __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const int32_t *seeds,
+                                  const uint32_t *__restrict__ new_of,
                                   uint32_t k, uint64_t *label, uint32_t *pred_arc,
                                   uint32_t *stamp_near, uint32_t tag0, uint32_t *q0,
                                   uint64_t *hq0, uint32_t heavy_cap, uint32_t n, Control *ctl) {
@@ -76,7 +77,7 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const in
         ctl->far_min[1] = INF32;
     }
     if (r >= k) return;
-    uint32_t s = (uint32_t)seeds[r];
+    uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
     label[s] = (uint64_t)r;               // distance 0, cell = rank r
     pred_arc[s] = SEED_ARC;
     stamp_near[s] = tag0;
@@ -599,10 +600,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
 __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
                               const uint64_t *__restrict__ label,
                               const uint32_t *__restrict__ pred_arc,
-                              const int32_t *__restrict__ seeds, int32_t *cell, uint32_t *dist,
+                              const int32_t *__restrict__ seeds,
+                              const uint32_t *__restrict__ orig_of, int32_t *cell, uint32_t *dist,
                               int32_t *pred) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint64_t lab = label[v];
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const uint32_t v = caller_id(orig_of, u);       // outputs are in the caller's ids
+        uint64_t lab = label[u];
         if (lab == INF64) {
             if (cell) cell[v] = -1;
             if (dist) dist[v] = INF32;
@@ -612,8 +615,9 @@ __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
         if (cell) cell[v] = seeds[(uint32_t)lab];
         if (dist) dist[v] = (uint32_t)(lab >> 32);
         if (pred) {
-            uint32_t pa = pred_arc[v];
-            pred[v] = pa == SEED_ARC ? (int32_t)v : (pa == INF32 ? -1 : (int32_t)adj[pa].x);
+            uint32_t pa = pred_arc[u];
+            pred[v] = pa == SEED_ARC ? (int32_t)v
+                                     : (pa == INF32 ? -1 : (int32_t)caller_id(orig_of, adj[pa].x));
         }
     }
 }
@@ -633,7 +637,7 @@ cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, cudaStream
     cudaError_t e = cudaMemsetAsync(ws.ctl, 0, sizeof(Control), s);
     if (e != cudaSuccess) return e;
     init_labels_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, ws.label, ws.pred_arc);
-    init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, ws.seeds, k, ws.label,
+    init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, ws.seeds, g.new_of, k, ws.label,
                                                        ws.pred_arc, ws.stamp_near,
                                                        ws.epoch_near, ws.q[0], ws.hq[0],
                                                        g.heavy_chunk_cap, g.n, ws.ctl);
@@ -683,7 +687,7 @@ cudaError_t launch_export(const DevGraph &g, Workspace &ws, uint32_t k, int32_t 
                           uint32_t *dist, int32_t *pred, cudaStream_t s) {
     (void)k;
     export_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.adj, ws.label, ws.pred_arc,
-                                                      ws.seeds, cell, dist, pred);
+                                                      ws.seeds, g.orig_of, cell, dist, pred);
     return cudaGetLastError();
 }
 

@@ -227,6 +227,39 @@ def test_light_heavy_arc_split_on_grid_and_hubs(delta, local):
         assert res.total == ref.total
 
 
+@pytest.mark.parametrize("relabel", ["0", "1"])
+def test_internal_vertex_order_is_invisible(relabel, monkeypatch):
+    """The library may renumber vertices internally (by descending degree);
+    forced off and on, every output stays in the caller's ids and arc
+    indices and equals the oracle: cells, distances, preds, the distance
+    graph with its tie-broken bridge arcs (small weights: many equal
+    bridges), the tree, and the batched path's trees."""
+    monkeypatch.setenv("STEINER_RELABEL", relabel)
+    cases = [(wl.rmat(12, 16, wmax=5, seed=31), 40), (wl.grid(120, 90, 1000, seed=32), 30),
+             (wl.rmat(12, 48, wmax=1000, seed=33), 25)]
+    for g, k in cases:
+        is_grid = g.n == 120 * 90
+        pool = np.arange(g.n, dtype=np.int32) if is_grid else wl.largest_cc(g)
+        seeds = wl.sample_distinct(pool, k, 34)
+        seeds2 = wl.sample_distinct(pool, k // 2 + 2, 35)
+        ref = oracle.steiner(g, seeds, want_labels=True, want_pairs=True)
+        ref2 = oracle.steiner(g, seeds2)
+        with st.SteinerGraph(g) as Gd:
+            rc, cell, dist, pred = Gd.voronoi(seeds)
+            res = Gd.query_detail(seeds)
+            rcb, batch = Gd.query_batch([seeds, seeds2])
+        assert rc == st.STEINER_OK and res.status == st.STEINER_OK and rcb == st.STEINER_OK
+        np.testing.assert_array_equal(cell, ref.cell)
+        np.testing.assert_array_equal(dist, ref.dist)
+        np.testing.assert_array_equal(pred, ref.pred)
+        np.testing.assert_array_equal(res.pairs[:, :4], ref.pairs)
+        np.testing.assert_array_equal(res.edges, ref.edges)
+        assert res.total == ref.total
+        for r, rf in zip(batch, (ref, ref2)):
+            np.testing.assert_array_equal(r.edges, rf.edges)
+            assert r.total == rf.total
+
+
 def test_iteration_cap_reports_timeout():
     """A loop cap that cannot be met returns STEINER_ETIMEOUT (bounded
     device loops; no hang) and the handle stays usable."""
