@@ -12,7 +12,13 @@
 //    slot admitted mid-run starts its own bands (continuous batching);
 //  * the persistent kernel can yield at an iteration boundary (a slot
 //    converged, or the host rang the doorbell), keeping all state in device
-//    memory, and resume later with more slots.
+//    memory, and resume later with more slots;
+//  * light and heavy arcs are split per slot as in the single-query kernel:
+//    while a slot's band iterates only arcs lighter than delta are relaxed,
+//    a per-vertex mask records which slots relaxed the vertex in their
+//    current band (vertices with any bit set are kept in a band list), and
+//    when a slot's near work drains its heavy arcs are relaxed once, in the
+//    next shared iteration, for the listed vertices with its bit.
 #include "multi.h"
 
 namespace stn {
@@ -33,13 +39,20 @@ struct MqArgs {
     uint64_t *item_pre;              // per item: (arc, slot) pairs before it in its block segment
     uint64_t *bsum;                  // per block: pairs in its segment
     uint32_t *far0, *far1;
+    unsigned long long *bmask;       // per vertex: slots that relaxed it in their current band
+    uint32_t *bl0, *bl1, *bl2;       // band lists
     MqControl *ctl;
     const uint32_t *doorbell;
     uint32_t delta;
     uint32_t base_near;
     uint32_t max_iters;
     uint32_t yield;          // leave once this many slots converged (0: only when all did)
+    uint32_t defer;          // light/heavy arc split on (some weight >= delta)
 };
+
+__device__ __forceinline__ uint32_t *band_list(const MqArgs &a, uint32_t i) {
+    return i == 0 ? a.bl0 : (i == 1 ? a.bl1 : a.bl2);
+}
 
 constexpr int MQ_WARPS = 256 / 32;
 constexpr int MQ_MAX_BLOCKS = 1024;
@@ -172,17 +185,23 @@ __device__ __forceinline__ void mq_push_near(const MqArgs &a, MqStage &st, const
 }
 
 // Relaxes up to MQ_ILP (arc, slot) pairs per lane.
+// Pair i is arc arc[i] for slot qs[i]; heavy[i] marks a heavy-arc pass
+// item (only arcs of weight >= delta), else only lighter arcs are relaxed
+// when the split is on.
 __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqTargets &t,
                                          const bool (&valid)[MQ_ILP],
                                          const uint32_t (&arc)[MQ_ILP],
                                          const uint32_t (&qs)[MQ_ILP],
                                          const uint64_t (&lab)[MQ_ILP],
+                                         const bool (&heavy)[MQ_ILP],
                                          unsigned long long &attempts,
                                          unsigned long long &improved) {
     uint2 e[MQ_ILP];
 #pragma unroll
-    for (int i = 0; i < MQ_ILP; ++i)
+    for (int i = 0; i < MQ_ILP; ++i) {
+        e[i] = make_uint2(0, 0);
         if (valid[i]) e[i] = __ldg(&a.adj[arc[i]]);
+    }
     uint64_t nd[MQ_ILP];
     bool imp[MQ_ILP];
 #pragma unroll
@@ -190,6 +209,7 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
         imp[i] = false;
         nd[i] = INF32;
         if (!valid[i] || lab[i] == INF64) continue;
+        if (heavy[i] ? e[i].y < a.delta : (a.defer && e[i].y >= a.delta)) continue;
         ++attempts;
         nd[i] = (lab[i] >> 32) + (uint64_t)e[i].y;
         if (nd[i] < INF32) {
@@ -248,6 +268,10 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
     uint32_t it = ldcg_u32(&ctl->it), fc = ldcg_u32(&ctl->fc);
     unsigned long long infl = __ldcg(&ctl->inflight) & ~__ldcg(&ctl->converged);
     unsigned long long conv_total = 0;
+    // heavy-arc passes: H = slots whose pass runs in this iteration
+    unsigned long long H = __ldcg(&ctl->hpass) & infl;
+    unsigned long long hp_done = __ldcg(&ctl->hp_done);
+    uint32_t bc = ldcg_u32(&ctl->blist);
     if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
     __syncthreads();
     uint32_t iters = 0, reason = 0;
@@ -256,10 +280,20 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         const uint32_t cs = it % 3, ns = (it + 1) % 3;
         const bool odd = it & 1;
         const uint32_t n_items = min(ldcg_u32(&ctl->near_count[cs]), a.n);
+        // Work items: the near frontier, then (when some slots run their
+        // heavy-arc pass) the band list.  A pass reads list bc and moves the
+        // survivors, with this iteration's new listings, to list bc + 1;
+        // list bc + 2 (read by the previous pass) is cleared for the next.
+        const uint32_t n_band = H ? min(ldcg_u32(&ctl->bcount[bc]), a.n) : 0u;
+        const uint32_t n_all = n_items + n_band;
+        const uint32_t tgt = H ? (bc + 1) % 3 : bc;
+        const uint32_t *blo = band_list(a, bc);
+        uint32_t *bln = band_list(a, tgt);
         if (first) {
             uint32_t r = (it + 2) % 3;
             ctl->near_count[r] = 0;
             ctl->act[r] = 0;
+            if (H) ctl->bcount[(bc + 2) % 3] = 0;
         }
         const uint32_t *qc = odd ? a.q1 : a.q0;
 
@@ -267,20 +301,34 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         // Phase A: every frontier vertex takes its pending slot mask; its
         // work is deg x |mask| (arc, slot) pairs; prefix sums per block
         // segment of the frontier.
-        const uint32_t seg = (n_items + gridDim.x - 1) / gridDim.x;
-        const uint32_t seg_lo = min(n_items, blockIdx.x * seg);
-        const uint32_t seg_hi = min(n_items, seg_lo + seg);
+        const uint32_t seg = (n_all + gridDim.x - 1) / gridDim.x;
+        const uint32_t seg_lo = min(n_all, blockIdx.x * seg);
+        const uint32_t seg_hi = min(n_all, seg_lo + seg);
         if (threadIdx.x == 0) st.carry = 0;
         __syncthreads();
         for (uint32_t b0 = seg_lo; b0 < seg_hi; b0 += blockDim.x) {
             uint32_t i = b0 + threadIdx.x;
             uint64_t w = 0;
+            bool listed = false;
+            uint32_t u = 0;
             if (i < seg_hi) {
-                uint32_t u = ldcg_u32(&qc[i]);
-                unsigned long long M = atomicExch(&a.nmask[u], 0ull);
+                unsigned long long M;
+                if (i < n_items) {
+                    u = ldcg_u32(&qc[i]);
+                    M = atomicExch(&a.nmask[u], 0ull);
+                    // first slot to relax u in its band lists u
+                    if (a.defer && M) listed = atomicOr(&a.bmask[u], M) == 0ull;
+                } else {
+                    u = ldcg_u32(&blo[i - n_items]);
+                    const unsigned long long old = atomicAnd(&a.bmask[u], ~H);
+                    M = old & H;                 // the slots whose band closes now
+                    listed = (old & ~H) != 0ull; // still in other slots' bands
+                }
                 a.item_mask[i] = M;
                 w = (uint64_t)(a.row_ptr[u + 1] - a.row_ptr[u]) * (uint64_t)popc64(M);
             }
+            const uint32_t ls = warp_append(listed, &ctl->bcount[tgt], a.n, &ctl->err);
+            if (ls != INF32) bln[ls] = u;
             uint64_t incl = block_inclusive_scan64(w, st.wtot);
             if (i < seg_hi) a.item_pre[i] = st.carry + incl - w;
             __syncthreads();
@@ -328,7 +376,7 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
             auto gpre = [&](uint32_t i) -> uint64_t {
                 return st.boff[i / seg] + __ldcg(reinterpret_cast<const unsigned long long *>(&a.item_pre[i]));
             };
-            uint32_t lo = 0, hi = n_items;          // first item: largest i with gpre(i) <= p
+            uint32_t lo = 0, hi = n_all;            // first item: largest i with gpre(i) <= p
             while (hi - lo > 1) {
                 uint32_t mid = lo + (hi - lo) / 2;
                 if (gpre(mid) <= p) lo = mid; else hi = mid;
@@ -339,22 +387,23 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                 uint64_t pre = ~0ull;
                 uint32_t u = 0, s0 = 0, c = 0;
                 unsigned long long M = 0;
-                if (idx < n_items) {
+                if (idx < n_all) {
                     pre = gpre(idx);
-                    u = ldcg_u32(&qc[idx]);
+                    u = idx < n_items ? ldcg_u32(&qc[idx]) : ldcg_u32(&blo[idx - n_items]);
                     M = __ldcg(&a.item_mask[idx]);
                     s0 = a.row_ptr[u];
                     c = (uint32_t)popc64(M);
                 }
-                const uint64_t wend = i0 + 32 < n_items ? gpre(i0 + 32) : W;
+                const bool hv = idx >= n_items;        // heavy-arc pass item
+                const uint64_t wend = i0 + 32 < n_all ? gpre(i0 + 32) : W;
                 const uint64_t stop = min(p1, wend);
                 const uint64_t pbase = __shfl_sync(FULL, pre, 0);
                 // window-relative prefixes fit 32 bits (an item has at most
                 // deg x 64 pairs)
-                const uint32_t rel = idx < n_items ? (uint32_t)(pre - pbase) : 0xFFFFFFFFu;
+                const uint32_t rel = idx < n_all ? (uint32_t)(pre - pbase) : 0xFFFFFFFFu;
                 const uint32_t q1 = M ? (uint32_t)(__ffsll((long long)M) - 1) : 0;   // lowest slot
                 for (; p < stop; p += 32 * MQ_ILP) {
-                    bool valid[MQ_ILP];
+                    bool valid[MQ_ILP], heavy[MQ_ILP];
                     uint32_t arc[MQ_ILP], qs[MQ_ILP];
                     uint64_t labs[MQ_ILP];
 #pragma unroll
@@ -369,6 +418,7 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                         const uint32_t co = __shfl_sync(FULL, c, owner);
                         const uint32_t qf = __shfl_sync(FULL, q1, owner);
                         const unsigned long long Mo = __shfl_sync(FULL, M, owner);
+                        heavy[k] = __shfl_sync(FULL, hv, owner);
                         const uint32_t local = pr - ro;
                         uint32_t j = local, q = qf;
                         if (valid[k] && co > 1) {            // several slots: split the index
@@ -379,7 +429,7 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                         arc[k] = so + j;
                         labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
                     }
-                    mq_relax(a, st, t, valid, arc, qs, labs, attempts, improved);
+                    mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
                 }
                 p = stop;
                 i0 += 32;
@@ -396,20 +446,28 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
             ctl->t_part[1] += tm2 - tm1;
             ctl->t_part[2] += tm3 - tm2;
             ctl->t_part[3] += tm4 - tm3;
-            ctl->items_total += n_items;
+            ctl->items_total += n_all;
             ctl->pairs_total += st.W;
         }
         ++it;
         ++iters;
+        if (H) bc = (bc + 1) % 3;
 
-        // per-slot decisions (every block computes the same from global state)
+        // per-slot decisions (every block computes the same from global
+        // state): a slot with near work queued continues its band; an idle
+        // one first runs its band's heavy-arc pass (next iteration), then is
+        // converged if nothing is parked far, else its far pile is split
         unsigned long long act_next = __ldcg(&ctl->act[it % 3]);
+        hp_done &= ~act_next;
         unsigned long long idle = infl & ~act_next, S = 0, conv = 0;
-        for (unsigned long long m = idle; m; m &= m - 1) {
+        H = a.defer ? (idle & ~hp_done) : 0ull;
+        hp_done |= H;
+        for (unsigned long long m = idle & ~H; m; m &= m - 1) {
             uint32_t q = __ffsll((long long)m) - 1;
             if (__ldcg(&ctl->far_pending[q]) <= 0) conv |= 1ull << q;
             else S |= 1ull << q;
         }
+        hp_done &= ~S;                      // a split opens a new band
         infl &= ~conv;
         conv_total |= conv;
         if (!infl) { reason = 1; break; }
@@ -512,6 +570,9 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
     if (first) {
         ctl->it = it;
         ctl->fc = fc;
+        ctl->hpass = H & infl;
+        ctl->hp_done = hp_done;
+        ctl->blist = bc;
         ctl->converged |= conv_total;
         ctl->iterations = iters;
         ctl->exit_reason = reason;
@@ -559,6 +620,8 @@ __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n,
         ctl->far_pending[q] = 0;
         atomicOr(&ctl->act[it % 3], bit);
         ctl->slot_overflow &= ~bit;
+        ctl->hp_done &= ~bit;
+        ctl->hpass &= ~bit;
     }
     if (r >= k) return;
     uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
@@ -705,28 +768,37 @@ cudaError_t mq_alloc(const DevGraph &g, MqState &m, cudaStream_t s) {
         MA(m.q[i], n);
         MA(m.far[i], n);
     }
-    MA(m.item_mask, n);
-    MA(m.item_pre, n);
+    MA(m.item_mask, 2 * (uint64_t)n);
+    MA(m.item_pre, 2 * (uint64_t)n);
+    MA(m.bmask, n);
+    for (int i = 0; i < 3; ++i) MA(m.bl[i], n);
     MA(m.bsum, MQ_MAX_BLOCKS);
     MA(m.ctl, 1);
     MA(m.d_pairtab, MQ_SLOTS);
     MA(m.d_k, MQ_SLOTS);
 #undef MA
-    if ((e = cudaMemsetAsync(m.nmask, 0, (size_t)n * 8, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.fmask, 0, (size_t)n * 8, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.stamp_near, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.in_far, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.ctl, 0, sizeof(MqControl), s)) != cudaSuccess) return e;
+    if ((e = mq_reset(m, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(m.d_pairtab, 0, MQ_SLOTS * sizeof(uint64_t *), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(m.d_k, 0, MQ_SLOTS * 4, s)) != cudaSuccess) return e;
     m.base_near = 1;
     return cudaSuccess;
 }
 
+cudaError_t mq_reset(MqState &m, cudaStream_t s) {
+    const size_t n = m.n;
+    cudaError_t e = cudaMemsetAsync(m.nmask, 0, n * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.fmask, 0, n * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.bmask, 0, n * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.stamp_near, 0, n * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.in_far, 0, n * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.ctl, 0, sizeof(MqControl), s);
+    return e;
+}
+
 void mq_free(MqState &m) {
     void *bufs[] = {m.label, m.pred, m.nmask, m.fmask, m.stamp_near, m.in_far, m.q[0], m.q[1],
                     m.item_mask, m.item_pre, m.bsum, m.far[0], m.far[1], m.ctl, m.d_pairtab,
-                    m.d_k};
+                    m.d_k, m.bmask, m.bl[0], m.bl[1], m.bl[2]};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (int q = 0; q < MQ_SLOTS; ++q) {
@@ -783,6 +855,11 @@ cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t d
     a.bsum = m.bsum;
     a.far0 = m.far[0];
     a.far1 = m.far[1];
+    a.bmask = m.bmask;
+    a.bl0 = m.bl[0];
+    a.bl1 = m.bl[1];
+    a.bl2 = m.bl[2];
+    a.defer = delta <= g.max_w ? 1u : 0u;
     a.ctl = m.ctl;
     a.doorbell = doorbell;
     a.delta = delta;

@@ -43,6 +43,11 @@ struct MqControl {
     unsigned long long t_part[5];
     unsigned long long items_total;     // frontier items visited
     unsigned long long pairs_total;     // (arc, slot) pairs relaxed
+    // light/heavy arc split, per slot (as in the single-query kernel)
+    unsigned long long hp_done;         // slots whose current band had its heavy-arc pass
+    unsigned long long hpass;           // slots whose heavy-arc pass runs in the next iteration
+    uint32_t blist;                     // band list receiving appends (rotates over 3)
+    uint32_t bcount[3];
 };
 
 struct MqState {
@@ -54,8 +59,10 @@ struct MqState {
     uint32_t *stamp_near = nullptr;         // n
     uint32_t *in_far = nullptr;             // n
     uint32_t *q[2] = {nullptr, nullptr};    // frontier, n
-    unsigned long long *item_mask = nullptr;    // n: slot mask taken by each frontier item
-    uint64_t *item_pre = nullptr;           // n: pair prefix within its block segment
+    unsigned long long *item_mask = nullptr;    // 2n: slot mask taken by each work item
+    uint64_t *item_pre = nullptr;           // 2n: pair prefix within its block segment
+    unsigned long long *bmask = nullptr;    // n: slots that relaxed v in their current band
+    uint32_t *bl[3] = {nullptr, nullptr, nullptr};  // band lists, n each
     uint64_t *bsum = nullptr;               // pairs per block segment
     uint32_t *far[2] = {nullptr, nullptr};  // n
     MqControl *ctl = nullptr;
@@ -84,6 +91,8 @@ cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uin
 cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
                            uint32_t max_iters, uint32_t yield, const uint32_t *doorbell,
                            cudaStream_t s);
+// Clears the shared frontier state (after an error).
+cudaError_t mq_reset(MqState &m, cudaStream_t s);
 // Predecessors and per-slot bridge tables for the slots in `slots`.
 cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slots,
                            cudaStream_t s);

@@ -159,3 +159,19 @@ def test_serving_budget_refusals():
         st.steiner_serve_stop(h)
     assert got[t_big][0] == st.STEINER_EBUSY
     assert got[t_ok][0] == st.STEINER_OK
+
+
+@pytest.mark.parametrize("batch_delta", [1, 100, 999])
+def test_batch_light_heavy_split(batch_delta):
+    """Band widths at or below the largest weight switch on the per-slot
+    light/heavy arc split of the batched kernel (heavy-arc passes of
+    different slots interleaved with other slots' bands); trees equal the
+    oracle's on a grid and on an R-MAT graph with hubs."""
+    for g, grid in ((wl.grid(160, 120, 1000, seed=47), True), (wl.rmat(12, 48, wmax=1000, seed=48), False)):
+        pool = np.arange(g.n, dtype=np.int32) if grid else wl.largest_cc(g)
+        qs = _queries(pool, [2, 9, 40, 3, 120, 17, 64, 5], 6 + batch_delta)
+        with st.SteinerGraph(g) as Gd:
+            Gd.set_param("batch_delta", batch_delta)
+            rc, res = Gd.query_batch(qs)
+        assert rc == st.STEINER_OK
+        _check(g, qs, res)
