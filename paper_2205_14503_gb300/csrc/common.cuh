@@ -90,6 +90,24 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, uint32_t *err) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Exchanges with release / acquire semantics at GPU scope.  A relaxation
+// that improves a label then release-exchanges the vertex's queue stamp; a
+// block taking the vertex from its staging buffer acquire-exchanges the
+// same stamp before reading the label.  Both are read-modify-writes of one
+// location, so either the taker's exchange reads a releaser's stamp (and
+// then sees that label), or the releaser's exchange reads the taker's
+// stamp (and queues the vertex again): no improvement is lost.
+__device__ __forceinline__ uint32_t exch_release(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t exch_acquire(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acquire.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

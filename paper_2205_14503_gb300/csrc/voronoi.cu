@@ -253,10 +253,10 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];   // independent of the exchange
             // with block-local rounds a staged vertex may be relaxed this very
-            // iteration: publish the label before reading its stamp (the
-            // local reader resets the stamp, fences, then reads the label)
-            if (a.local_rounds) __threadfence();
-            to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
+            // iteration: the stamp exchange releases the label (the local
+            // reader acquire-exchanges the stamp, then reads the label)
+            to_near[u] = (a.local_rounds ? exch_release(&a.stamp_near[v], t.tag_next)
+                                         : atomicExch(&a.stamp_near[v], t.tag_next)) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
             cand[u] = true;
@@ -442,8 +442,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                     uint64_t lab = INF64;
                     if (has) {
                         u = st.near_buf[i];
-                        atomicExch(&a.stamp_near[u], tag_cur);     // later improvements re-push u
-                        __threadfence();
+                        exch_acquire(&a.stamp_near[u], tag_cur);   // later improvements re-push u
                         s = a.row_ptr[u];
                         deg = a.row_ptr[u + 1] - s;
                         lab = ldcg_u64(&a.label[u]);
