@@ -188,6 +188,13 @@ void advance_epochs(Workspace &ws, const Control &c, cudaStream_t s) {
     }
 }
 
+// Partition failures are not fatal: the kernels then filter arcs by weight
+// on the id-sorted rows.
+cudaError_t ensure_partition(steiner_graph *G, uint32_t delta) {
+    if (ensure_partition_dev(G->g, delta, G->stream) != cudaSuccess) G->g.part_delta = 0;
+    return cudaSuccess;
+}
+
 // Runs Steps 1 (and, with `full`, 2-7) of Algorithm 2 for one sorted seed
 // list.  Leaves the control block in G->h_ctl.
 int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, float *ms) {
@@ -202,7 +209,8 @@ int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, fl
     SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
                  ws.epoch_band};
     CK(cudaEventRecord(G->ev[0], s));
-    CK(launch_init(G->g, ws, k, s));
+    CK(ensure_partition(G, G->delta));
+    CK(launch_init(G->g, ws, k, G->delta, s));
     CK(cudaEventRecord(G->ev[1], s));
     CK(launch_sssp(G->g, ws, G->geo, p, s));
     CK(cudaEventRecord(G->ev[2], s));
@@ -506,7 +514,8 @@ void steiner_free_graph(steiner_graph_t G) {
                     ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
                     ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
                     ws.best, ws.tree_key, ws.tree_key2, ws.tree_w, ws.tree_w2, G->g.row_ptr,
-                    G->g.adj, G->g.heavy_chunks, G->g.orig_row_ptr, G->g.orig_of, G->g.new_of};
+                    G->g.adj, G->g.heavy_chunks, G->g.orig_row_ptr, G->g.orig_of, G->g.new_of,
+                    G->g.adj_w, G->g.lend};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (auto &ev : G->ev)
@@ -672,6 +681,9 @@ int api_device(steiner_graph *G) { return G->device; }
 BatchEngine *&api_batch(steiner_graph *G) { return G->batch; }
 ServeEngine *&api_serve(steiner_graph *G) { return G->serve; }
 uint32_t api_delta(steiner_graph *G) { return G->delta; }
+void api_ensure_partition(steiner_graph *G, uint32_t delta) {
+    ensure_partition_dev(G->g, delta, G->stream);
+}
 uint32_t api_nbits(steiner_graph *G) { return G->nbits; }
 const Geometry &api_geometry(steiner_graph *G) { return G->geo; }
 void api_set_error(const std::string &msg) { g_last_error = msg; }

@@ -23,6 +23,8 @@ int api_device(steiner_graph *G);
 BatchEngine *&api_batch(steiner_graph *G);
 ServeEngine *&api_serve(steiner_graph *G);
 uint32_t api_delta(steiner_graph *G);
+// Builds the weight-partitioned rows for band width delta if needed.
+void api_ensure_partition(steiner_graph *G, uint32_t delta);
 uint32_t api_nbits(steiner_graph *G);
 const Geometry &api_geometry(steiner_graph *G);
 void api_set_error(const std::string &msg);

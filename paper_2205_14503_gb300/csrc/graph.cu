@@ -79,6 +79,62 @@ __global__ void __launch_bounds__(256) validate_kernel(const uint32_t *__restric
     if (lane == 0 && wmax) atomicMax(max_w, wmax);
 }
 
+// One warp per row: arcs lighter than delta first, then the rest, each part
+// in the row's order.
+__global__ void __launch_bounds__(256) partition_kernel(const uint32_t *__restrict__ row_ptr,
+                                                        const uint2 *__restrict__ adj, uint32_t n,
+                                                        uint32_t delta, uint2 *__restrict__ adj_w,
+                                                        uint32_t *__restrict__ lend) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t v = warp; v < n; v += nwarps) {
+        const uint32_t s = row_ptr[v], e = row_ptr[v + 1];
+        uint32_t nl = 0;
+        for (uint32_t b = s; b < e; b += 32) {
+            const uint32_t j = b + lane;
+            nl += __popc(__ballot_sync(FULL, j < e && __ldg(&adj[j].y) < delta));
+        }
+        if (lane == 0) lend[v] = s + nl;
+        uint32_t lo = s, hi = s + nl;
+        for (uint32_t b = s; b < e; b += 32) {
+            const uint32_t j = b + lane;
+            const bool valid = j < e;
+            const uint2 x = valid ? __ldg(&adj[j]) : make_uint2(0, 0);
+            const bool light = valid && x.y < delta;
+            const uint32_t ml = __ballot_sync(FULL, light), mv = __ballot_sync(FULL, valid);
+            const uint32_t mh = mv & ~ml, lt = lanemask_lt();
+            if (light) adj_w[lo + __popc(ml & lt)] = x;
+            else if (valid) adj_w[hi + __popc(mh & lt)] = x;
+            lo += __popc(ml);
+            hi += __popc(mh);
+        }
+    }
+}
+
+cudaError_t launch_partition(const DevGraph &g, uint32_t delta, cudaStream_t s) {
+    uint64_t blocks = ((uint64_t)g.n + 7) / 8;
+    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    if (blocks < 1) blocks = 1;
+    partition_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.n, delta, g.adj_w, g.lend);
+    return cudaGetLastError();
+}
+
+cudaError_t ensure_partition_dev(DevGraph &g, uint32_t delta, cudaStream_t s) {
+    if (delta > g.max_w || g.m == 0 || g.part_delta == delta) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!g.adj_w) e = cudaMalloc((void **)&g.adj_w, (size_t)g.m * sizeof(uint2));
+    if (e == cudaSuccess && !g.lend) e = cudaMalloc((void **)&g.lend, (size_t)g.n * 4);
+    if (e == cudaSuccess) e = launch_partition(g, delta, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g.part_delta = 0;
+        return e;
+    }
+    g.part_delta = delta;
+    return cudaSuccess;
+}
+
 cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,
                                   uint32_t n, uint64_t m, uint2 *adj, const uint32_t *new_of,
                                   const uint32_t *new_row_ptr, uint32_t *bad, uint32_t *max_w,

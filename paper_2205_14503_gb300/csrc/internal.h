@@ -32,7 +32,20 @@ struct DevGraph {
     uint32_t *orig_of = nullptr;     // internal id -> caller id, n
     uint32_t *new_of = nullptr;      // caller id -> internal id, n
     uint32_t *orig_row_ptr = nullptr;   // the caller's row offsets, n + 1
+    // Weight-partitioned copy of adj for the Voronoi kernels (built for one
+    // band width at a time): row v holds its arcs lighter than part_delta
+    // in [row_ptr[v], lend[v]) and the rest in [lend[v], row_ptr[v + 1]).
+    // The id-sorted adj stays the reference for pred, bridges and the tree.
+    uint2 *adj_w = nullptr;
+    uint32_t *lend = nullptr;
+    uint32_t part_delta = 0;        // 0: not built
 };
+
+// The weight-partitioned rows to use for band width delta: built for that
+// width and the split on (delta at or below the largest weight), else null.
+inline const uint32_t *active_lend(const DevGraph &g, uint32_t delta) {
+    return (delta <= g.max_w && g.adj_w && g.lend && g.part_delta == delta) ? g.lend : nullptr;
+}
 
 // Caller's arc index of internal arc `arc` of internal row v starting at rs.
 __device__ __forceinline__ uint32_t caller_arc(const uint32_t *orig_of, const uint32_t *orig_row_ptr,
@@ -137,7 +150,8 @@ struct SsspParams {
 };
 
 // voronoi.cu
-cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, cudaStream_t s);
+cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t delta,
+                        cudaStream_t s);
 cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
                         const SsspParams &p, cudaStream_t s);
 cudaError_t launch_export(const DevGraph &g, Workspace &ws, uint32_t k, int32_t *cell,
@@ -156,6 +170,14 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
 int mst_occupancy(int threads);
 
 // graph.cu
+// Builds g.adj_w / g.lend for band width delta (both allocated by the caller).
+cudaError_t launch_partition(const DevGraph &g, uint32_t delta, cudaStream_t s);
+// With the light/heavy split on for band width delta (delta at or below the
+// largest weight), the Voronoi kernels read rows partitioned by weight
+// class: allocates and builds (or rebuilds, after a change of delta) that
+// copy.  On failure part_delta is 0 and the kernels filter arcs by weight
+// on the id-sorted rows instead.
+cudaError_t ensure_partition_dev(DevGraph &g, uint32_t delta, cudaStream_t s);
 // Validates the caller's CSR (row_ptr, col, w) and writes the interleaved
 // internal adjacency: arc e of caller row u goes to
 // new_row_ptr[new_of[u]] + (e - row_ptr[u]) with neighbour new_of[col[e]]

@@ -48,6 +48,9 @@ struct MqArgs {
     uint32_t max_iters;
     uint32_t yield;          // leave once this many slots converged (0: only when all did)
     uint32_t defer;          // light/heavy arc split on (some weight >= delta)
+    // with the split: end of each row's light part in the weight-partitioned
+    // adjacency `adj` (null: rows are unpartitioned and arcs are filtered)
+    const uint32_t *lend;
 };
 
 __device__ __forceinline__ uint32_t *band_list(const MqArgs &a, uint32_t i) {
@@ -69,6 +72,7 @@ struct MqStage {
     unsigned long long Tnew[MQ_SLOTS];     // thresholds after a split
     uint32_t fmin[MQ_SLOTS];               // far-distance minimum of this segment
     int32_t fpend[MQ_SLOTS];               // change of far_pending in this segment
+    unsigned long long mag[MQ_SLOTS + 1];  // ceil(2^40 / c) for c = 2..64 (divmod by c)
 };
 
 struct MqTargets {
@@ -273,6 +277,10 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
     unsigned long long hp_done = __ldcg(&ctl->hp_done);
     uint32_t bc = ldcg_u32(&ctl->blist);
     if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
+    if (threadIdx.x <= MQ_SLOTS) {
+        const uint32_t c = threadIdx.x;
+        st.mag[c] = c > 1 ? ((1ull << 40) + c - 1) / c : 0ull;
+    }
     __syncthreads();
     uint32_t iters = 0, reason = 0;
 
@@ -325,7 +333,11 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                     listed = (old & ~H) != 0ull; // still in other slots' bands
                 }
                 a.item_mask[i] = M;
-                w = (uint64_t)(a.row_ptr[u + 1] - a.row_ptr[u]) * (uint64_t)popc64(M);
+                // frontier items relax the light part, band items the heavy one
+                const uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
+                const uint32_t le = a.lend ? a.lend[u] : r1;
+                const uint32_t deg = i < n_items ? le - r0 : (a.lend ? r1 - le : r1 - r0);
+                w = (uint64_t)deg * (uint64_t)popc64(M);
             }
             const uint32_t ls = warp_append(listed, &ctl->bcount[tgt], a.n, &ctl->err);
             if (ls != INF32) bln[ls] = u;
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                     pre = gpre(idx);
                     u = idx < n_items ? ldcg_u32(&qc[idx]) : ldcg_u32(&blo[idx - n_items]);
                     M = __ldcg(&a.item_mask[idx]);
-                    s0 = a.row_ptr[u];
+                    s0 = (idx >= n_items && a.lend) ? a.lend[u] : a.row_ptr[u];
                     c = (uint32_t)popc64(M);
                 }
                 const bool hv = idx >= n_items;        // heavy-arc pass item
@@ -401,33 +413,67 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                 // window-relative prefixes fit 32 bits (an item has at most
                 // deg x 64 pairs)
                 const uint32_t rel = idx < n_all ? (uint32_t)(pre - pbase) : 0xFFFFFFFFu;
-                const uint32_t q1 = M ? (uint32_t)(__ffsll((long long)M) - 1) : 0;   // lowest slot
+                // pair index -> (arc j, slot t) = divmod(local, c): multiply by
+                // ceil(2^40 / c), exact for local < 2^32 and c <= 64
+                const uint64_t mag = st.mag[c];
                 for (; p < stop; p += 32 * MQ_ILP) {
                     bool valid[MQ_ILP], heavy[MQ_ILP];
                     uint32_t arc[MQ_ILP], qs[MQ_ILP];
                     uint64_t labs[MQ_ILP];
+                    const uint64_t plast = min(p + 32 * MQ_ILP, stop) - 1;
+                    const uint32_t ow0 = warp_owner_search(rel, (uint32_t)(p - pbase));
+                    const uint32_t owl = warp_owner_search(rel, (uint32_t)(plast - pbase));
+                    if (ow0 == owl) {
+                        // the whole round lies in one item (dense masks, long
+                        // rows): its fields once, no per-pair owner search
+                        const uint32_t ro = __shfl_sync(FULL, rel, ow0);
+                        const uint32_t so = __shfl_sync(FULL, s0, ow0);
+                        const uint32_t uo = __shfl_sync(FULL, u, ow0);
+                        const uint32_t co = __shfl_sync(FULL, c, ow0);
+                        const unsigned long long Mo = __shfl_sync(FULL, M, ow0);
+                        const uint64_t mo = __shfl_sync(FULL, mag, ow0);
+                        const bool ho = __shfl_sync(FULL, hv, ow0);
 #pragma unroll
-                    for (int k = 0; k < MQ_ILP; ++k) {
-                        const uint64_t pp = p + lane + 32 * k;
-                        valid[k] = pp < stop;
-                        const uint32_t pr = valid[k] ? (uint32_t)(pp - pbase) : 0;
-                        const uint32_t owner = warp_owner_search(rel, pr);
-                        const uint32_t ro = __shfl_sync(FULL, rel, owner);
-                        const uint32_t so = __shfl_sync(FULL, s0, owner);
-                        const uint32_t uo = __shfl_sync(FULL, u, owner);
-                        const uint32_t co = __shfl_sync(FULL, c, owner);
-                        const uint32_t qf = __shfl_sync(FULL, q1, owner);
-                        const unsigned long long Mo = __shfl_sync(FULL, M, owner);
-                        heavy[k] = __shfl_sync(FULL, hv, owner);
-                        const uint32_t local = pr - ro;
-                        uint32_t j = local, q = qf;
-                        if (valid[k] && co > 1) {            // several slots: split the index
-                            j = local / co;
-                            q = nth_bit64(Mo, local - j * co);
+                        for (int k = 0; k < MQ_ILP; ++k) {
+                            const uint64_t pp = p + lane + 32 * k;
+                            valid[k] = pp < stop;
+                            heavy[k] = ho;
+                            const uint32_t local = valid[k] ? (uint32_t)(pp - pbase) - ro : 0;
+                            uint32_t j = local, tq = 0;
+                            if (co > 1) {
+                                j = (uint32_t)__umul64hi((uint64_t)local, mo << 24);
+                                tq = local - j * co;
+                            }
+                            const uint32_t q = co == MQ_SLOTS ? tq : nth_bit64(Mo, tq);
+                            qs[k] = q;
+                            arc[k] = so + j;
+                            labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
                         }
-                        qs[k] = q;
-                        arc[k] = so + j;
-                        labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < MQ_ILP; ++k) {
+                            const uint64_t pp = p + lane + 32 * k;
+                            valid[k] = pp < stop;
+                            const uint32_t pr = valid[k] ? (uint32_t)(pp - pbase) : 0;
+                            const uint32_t owner = warp_owner_search(rel, pr);
+                            const uint32_t ro = __shfl_sync(FULL, rel, owner);
+                            const uint32_t so = __shfl_sync(FULL, s0, owner);
+                            const uint32_t uo = __shfl_sync(FULL, u, owner);
+                            const uint32_t co = __shfl_sync(FULL, c, owner);
+                            const unsigned long long Mo = __shfl_sync(FULL, M, owner);
+                            const uint64_t mo = __shfl_sync(FULL, mag, owner);
+                            heavy[k] = __shfl_sync(FULL, hv, owner);
+                            const uint32_t local = pr - ro;
+                            uint32_t j = local, tq = 0;
+                            if (valid[k] && co > 1) {        // several slots: split the index
+                                j = (uint32_t)__umul64hi((uint64_t)local, mo << 24);
+                                tq = local - j * co;
+                            }
+                            const uint32_t q = co == MQ_SLOTS ? tq : nth_bit64(Mo, tq);
+                            qs[k] = q;
+                            arc[k] = so + j;
+                            labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
+                        }
                     }
                     mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
                 }
@@ -860,6 +906,8 @@ cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t d
     a.bl1 = m.bl[1];
     a.bl2 = m.bl[2];
     a.defer = delta <= g.max_w ? 1u : 0u;
+    a.lend = active_lend(g, delta);
+    if (a.lend) a.adj = g.adj_w;        // rows partitioned by weight class
     a.ctl = m.ctl;
     a.doorbell = doorbell;
     a.delta = delta;

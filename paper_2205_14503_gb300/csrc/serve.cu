@@ -222,6 +222,7 @@ struct BatchEngine {
         h_masks[0] = inflight;
         h_masks[1] = 0;
         delta = cur_delta();
+        api_ensure_partition(G, delta);
         cudaError_t e = cudaMemcpyAsync(&m.ctl->inflight, &h_masks[0], 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&m.ctl->converged, &h_masks[1], 8, cudaMemcpyHostToDevice, s);

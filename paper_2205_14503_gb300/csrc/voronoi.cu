@@ -51,6 +51,9 @@ struct SsspArgs {
     uint64_t *band_hq;       // heavy-row chunks of listed high-degree vertices
     uint32_t base_band;
     uint32_t defer;          // light/heavy arc split on
+    // with the split: end of each row's light part in the weight-partitioned
+    // adjacency `adj` (null: rows are unpartitioned and arcs are filtered)
+    const uint32_t *lend;
 };
 
 // ---------------------------------------------------------------------------
@@ -66,7 +69,8 @@ __global__ void init_labels_kernel(uint32_t n, uint64_t *__restrict__ label,
     }
 }
 
-__global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const int32_t *seeds,
+__global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr,
+                                  const uint32_t *__restrict__ lend, const int32_t *seeds,
                                   const uint32_t *__restrict__ new_of,
                                   uint32_t k, uint64_t *label, uint32_t *pred_arc,
                                   uint32_t *stamp_near, uint32_t tag0, uint32_t *q0,
@@ -81,7 +85,7 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr, const in
     label[s] = (uint64_t)r;               // distance 0, cell = rank r
     pred_arc[s] = SEED_ARC;
     stamp_near[s] = tag0;
-    uint32_t rs = row_ptr[s], deg = row_ptr[s + 1] - rs;
+    uint32_t rs = row_ptr[s], deg = (lend ? lend[s] : row_ptr[s + 1]) - rs;   // near part
     if (deg >= HEAVY_DEG) {
         uint32_t nc = (deg + CHUNK - 1) / CHUNK;
         uint32_t base = atomicAdd(&ctl->heavy_count[0], nc);
@@ -251,7 +255,8 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         ++improved;
         uint32_t v = e[u].x;
         if (nd[u] < t.T) {
-            uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];   // independent of the exchange
+            uint32_t r0 = a.row_ptr[v];                           // independent of the exchange
+            uint32_t r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
             // with block-local rounds a staged vertex may be relaxed this very
             // iteration: the stamp exchange releases the label (the local
             // reader acquire-exchanges the stamp, then reads the label)
@@ -270,18 +275,32 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
     }
 }
 
-// Lists vertex u (lanes with `want`) in the current band once.
-__device__ __forceinline__ void band_track(const SsspArgs &a, bool want, uint32_t u, uint32_t tag) {
-    bool add = want && atomicExch(&a.stamp_band[u], tag) != tag;
-    uint32_t slot = warp_append(add, &a.ctl->band_count, a.n, &a.ctl->err);
+// Lists vertex u (lanes with `want`; hdeg arcs in its heavy part) in the
+// current band once: as one item, or as CHUNK-arc pieces when the heavy
+// part is long.  A vertex without heavy arcs needs no listing.
+__device__ __forceinline__ void band_track(const SsspArgs &a, bool want, uint32_t u, uint32_t hdeg,
+                                           uint32_t tag) {
+    bool add = want && hdeg > 0 && atomicExch(&a.stamp_band[u], tag) != tag;
+    const bool big = add && hdeg >= HEAVY_DEG;
+    uint32_t slot = warp_append(add && !big, &a.ctl->band_count, a.n, &a.ctl->err);
     if (slot != INF32) a.band_q[slot] = u;
+    if (big) {
+        const uint32_t nc = (hdeg + CHUNK - 1) / CHUNK;
+        const uint32_t base = atomicAdd(&a.ctl->band_hcount, nc);
+        if (base + nc > a.heavy_cap || base + nc < base) {
+            atomicOr(&a.ctl->err, ERR_CAPACITY);
+        } else {
+            for (uint32_t c = 0; c < nc; ++c) a.band_hq[base + c] = ((uint64_t)u << 32) | c;
+        }
+    }
 }
 
-// Lists high-degree vertex u (warp-uniform) in the current band once, as
-// its CHUNK-arc pieces.
+// Lists high-degree vertex u (warp-uniform; deg arcs in its heavy part) in
+// the current band once, as its CHUNK-arc pieces.
 __device__ __forceinline__ void band_track_heavy(const SsspArgs &a, uint32_t u, uint32_t deg,
                                                  uint32_t tag) {
     const uint32_t lane = lane_id();
+    if (deg == 0) return;
     uint32_t add = 0;
     if (lane == 0) add = atomicExch(&a.stamp_band[u], tag) != tag;
     if (!__shfl_sync(FULL, add, 0)) return;
@@ -366,10 +385,13 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 uint64_t item = __ldcg(reinterpret_cast<const unsigned long long *>(&hqc[wi]));
                 uint32_t u = (uint32_t)(item >> 32), c = (uint32_t)item;
                 uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
-                uint32_t s = r0 + c * CHUNK;
-                uint32_t e = min(r1, s + CHUNK);
+                const uint32_t le = a.lend ? a.lend[u] : r1;      // light part [r0, le)
+                // a band's heavy pass covers the heavy part, else the light one
+                const uint32_t base = hp && a.lend ? le : r0, end = hp ? r1 : le;
+                uint32_t s = base + c * CHUNK;
+                uint32_t e = min(end, s + CHUNK);
                 uint64_t lab = ldcg_u64(&a.label[u]);
-                if (track && c == 0) band_track_heavy(a, u, r1 - r0, tag_band);
+                if (track && c == 0) band_track_heavy(a, u, a.lend ? r1 - le : r1 - r0, tag_band);
                 for (uint32_t b = s; b < e; b += 32 * ILP) {
                     bool valid[ILP];
                     uint32_t arc[ILP];
@@ -387,16 +409,24 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
                 uint32_t i = (wi - n_heavy) * bsz + lane;
                 bool has = lane < bsz && i < n_light;
-                uint32_t s = 0, deg = 0, u = 0;
+                uint32_t s = 0, deg = 0, u = 0, hdeg = 0;
                 uint64_t lab = INF64;
                 if (has) {
                     u = ldcg_u32(&qc[i]);
-                    s = a.row_ptr[u];
-                    deg = a.row_ptr[u + 1] - s;
+                    const uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
+                    const uint32_t le = a.lend ? a.lend[u] : r1;
+                    if (hp) {                       // the heavy part (or the whole row)
+                        s = a.lend ? le : r0;
+                        deg = r1 - s;
+                    } else {                        // the light part
+                        s = r0;
+                        deg = le - r0;
+                        hdeg = a.lend ? r1 - le : r1 - r0;
+                    }
                     lab = ldcg_u64(&a.label[u]);
                     if (lab == INF64) deg = 0;
                 }
-                if (track) band_track(a, has, u, tag_band);
+                if (track) band_track(a, has, u, hdeg, tag_band);
                 uint32_t incl = warp_inclusive_scan(deg);
                 uint32_t excl = incl - deg;
                 uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -438,16 +468,19 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 for (uint32_t b0 = wib * lbsz; b0 < cnt; b0 += nwb * lbsz) {
                     uint32_t i = lo + b0 + lane;
                     bool has = lane < lbsz && b0 + lane < cnt;
-                    uint32_t s = 0, deg = 0, u = 0;
+                    uint32_t s = 0, deg = 0, u = 0, hdeg = 0;
                     uint64_t lab = INF64;
                     if (has) {
                         u = st.near_buf[i];
                         exch_acquire(&a.stamp_near[u], tag_cur);   // later improvements re-push u
                         s = a.row_ptr[u];
-                        deg = a.row_ptr[u + 1] - s;
+                        const uint32_t r1 = a.row_ptr[u + 1];
+                        const uint32_t le = a.lend ? a.lend[u] : r1;
+                        deg = le - s;
+                        hdeg = a.lend ? r1 - le : r1 - s;
                         lab = ldcg_u64(&a.label[u]);
                     }
-                    if (track) band_track(a, has, u, tag_band);
+                    if (track) band_track(a, has, u, hdeg, tag_band);
                     uint32_t incl = warp_inclusive_scan(deg);
                     uint32_t excl = incl - deg;
                     uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -549,7 +582,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             bool to_near = valid && d >= T_old && d < T;     // below T_old: already settled
             bool keep = valid && d >= T;
             if (to_near) {
-                uint32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
+                uint32_t r0 = a.row_ptr[v], r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];
                 to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
                 deg = r1 - r0;
             }
@@ -632,11 +665,13 @@ static int grid_for(uint64_t items, int threads) {
     return (int)b;
 }
 
-cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, cudaStream_t s) {
+cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t delta,
+                        cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ws.ctl, 0, sizeof(Control), s);
     if (e != cudaSuccess) return e;
     init_labels_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, ws.label, ws.pred_arc);
-    init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, ws.seeds, g.new_of, k, ws.label,
+    init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, active_lend(g, delta), ws.seeds,
+                                                       g.new_of, k, ws.label,
                                                        ws.pred_arc, ws.stamp_near,
                                                        ws.epoch_near, ws.q[0], ws.hq[0],
                                                        g.heavy_chunk_cap, g.n, ws.ctl);
@@ -677,6 +712,8 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.band_hq = ws.band_hq;
     a.base_band = p.base_band;
     a.defer = p.delta <= g.max_w ? 1u : 0u;
+    a.lend = active_lend(g, p.delta);
+    if (a.lend) a.adj = g.adj_w;        // rows partitioned by weight class
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(geo.sssp_blocks),
                                        dim3(geo.threads), args, 0, s);
