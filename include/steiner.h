@@ -196,8 +196,8 @@ int steiner_serve_stop(steiner_graph_t g);
  *   "local_rounds" block-local relaxation rounds per frontier iteration
  *                  (0 = off): a block keeps relaxing the vertices it just
  *                  queued, a hop per round, before the grid barrier
- *   "batch_delta"  band width of the multi-query engine (0 = "delta" raised
- *                  above the largest weight, so no light/heavy split)
+ *   "batch_delta"  band width of the multi-query engine (0 = w_max / 8 when
+ *                  "delta" is at most the largest weight w_max, else "delta")
  *   "batch_yield_div"  a serving launch returns to the host (to retire and
  *                  admit) once 1/batch_yield_div of its in-flight queries
  *                  converged (1..64, default 1: whole waves), or earlier

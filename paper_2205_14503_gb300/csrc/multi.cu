@@ -376,24 +376,36 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         t.fmin = ctl->fmin[fc];
         t.tag_next = a.base_near + it + 1;
 
-        // Phase B: warp w relaxes pairs [W w / nw, W (w + 1) / nw), numbered
-        // arc-major inside each item (arc j, slot t -> j * |mask| + t).  The
-        // warp slides a window of 32 consecutive frontier items (one per
-        // lane, loaded in parallel) and spreads the window's pairs over its
-        // lanes, 4 per lane in flight.
+        // Phase B: the W (arc, slot) pairs, numbered arc-major inside each
+        // item (arc j, slot t -> j * |mask| + t), are cut into 32 chunks per
+        // warp, and warp w takes chunks w, w + nw, w + 2 nw, ... spread over
+        // the whole pair space, so a costly region (many improving pairs) is
+        // shared by many warps.  Lane i finds the first item of the warp's
+        // i-th chunk (all 32 searches at once).  Inside a chunk the warp
+        // slides a window of 32 consecutive items (one per lane, loaded in
+        // parallel) and spreads the window's pairs over its lanes, 4 per lane
+        // in flight.
         const uint64_t W = st.W;
-        uint64_t p = (uint64_t)((unsigned __int128)W * warp / nwarps);
-        const uint64_t p1 = (uint64_t)((unsigned __int128)W * (warp + 1) / nwarps);
-        if (p < p1) {
-            auto gpre = [&](uint32_t i) -> uint64_t {
-                return st.boff[i / seg] + __ldcg(reinterpret_cast<const unsigned long long *>(&a.item_pre[i]));
-            };
+        auto gpre = [&](uint32_t i) -> uint64_t {
+            return st.boff[i / seg] + __ldcg(reinterpret_cast<const unsigned long long *>(&a.item_pre[i]));
+        };
+        const uint64_t n_chunks = (uint64_t)nwarps * 32;
+        const uint64_t my_chunk = warp + (uint64_t)lane * nwarps;
+        const uint64_t my_p = (uint64_t)((unsigned __int128)W * my_chunk / n_chunks);
+        const uint64_t my_p1 = (uint64_t)((unsigned __int128)W * (my_chunk + 1) / n_chunks);
+        uint32_t my_i0 = 0;
+        if (my_p < my_p1) {
             uint32_t lo = 0, hi = n_all;            // first item: largest i with gpre(i) <= p
             while (hi - lo > 1) {
                 uint32_t mid = lo + (hi - lo) / 2;
-                if (gpre(mid) <= p) lo = mid; else hi = mid;
+                if (gpre(mid) <= my_p) lo = mid; else hi = mid;
             }
-            uint32_t i0 = lo;
+            my_i0 = lo;
+        }
+        for (uint32_t ch = 0; ch < 32; ++ch) {
+            uint64_t p = __shfl_sync(FULL, my_p, ch);
+            const uint64_t p1 = __shfl_sync(FULL, my_p1, ch);
+            uint32_t i0 = __shfl_sync(FULL, my_i0, ch);
             while (p < p1) {
                 uint32_t idx = i0 + lane;
                 uint64_t pre = ~0ull;
