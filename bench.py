@@ -352,8 +352,17 @@ def run_batch_mode(args, world, rank, local):
     import paper_2205_14503_gb300.workloads as wl
     from paper_2205_14503_gb300 import steiner as st
     torch.cuda.set_device(local)
-    g = wl.config_graph(4)
-    qs = wl.config_seed_sets(4, g)
+    if args.batch_scale:
+        # profiling only: an R-MAT graph of another scale, same query recipe
+        c = wl.CONFIGS[4]
+        g = wl.rmat(args.batch_scale, 16, (0.57, 0.19, 0.19), c["wmax"], wl.CONFIG_SEED + 4, True)
+        pool = wl.largest_cc(g)
+        ks = wl.log_uniform_sizes(c["queries"], c["klo"], c["khi"], (wl.CONFIG_SEED + 4) ^ 0x517E)
+        qs = [wl.sample_distinct(pool, int(k), (wl.CONFIG_SEED + 4 + 0xC0FFEE) + 7919 * i)
+              for i, k in enumerate(ks)]
+    else:
+        g = wl.config_graph(4)
+        qs = wl.config_seed_sets(4, g)
     if rank > 0:
         pool = wl.largest_cc(g)
         qs = [wl.sample_distinct(pool, q.size, 0x5EED + 4000 + 97 * rank + i) for i, q in enumerate(qs)]
@@ -391,7 +400,8 @@ def run_batch_mode(args, world, rank, local):
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_batch,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": "rmat22_batch64", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
+            "config": {"workload": f"rmat{args.batch_scale or 22}_batch64", "n": g.n,
+                       "arcs": g.n_arcs, "queries": len(qs),
                        "k_range": [3, 1000],
                        "tuned": {k: tuned[k] for k in ("delta", "sssp_blocks", "local_rounds")}
                        if tuned else None},
@@ -548,6 +558,8 @@ def main():
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3],
                     help="plain mode: single-query workload (2 = the 4096^2 grid, the default; "
                          "1 = R-MAT 16, 3 = R-MAT 26, use with --no-cpu-baseline)")
+    ap.add_argument("--batch-scale", type=int, default=None,
+                    help="batch mode, profiling only: R-MAT scale instead of 22")
     ap.add_argument("--with-large", action="store_true",
                     help="ablation mode: include the R-MAT scale-26 workload")
     ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation"], default="plain",
