@@ -70,7 +70,7 @@ def apply_cached(G: "st.SteinerGraph", graph, cache_path: str = DEFAULT_CACHE,
     return entry
 
 
-def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.125, 0.5, 1, 2),
+def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.125, 0.25, 0.5, 1, 2),
          block_fractions=(0.5, 1.0), local_rounds=(0, 32), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
     """Times the Voronoi kernel over a grid of (delta, blocks, block-local
