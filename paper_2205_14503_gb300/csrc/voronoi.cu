@@ -104,6 +104,8 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr,
 
 constexpr int ILP = 4;                 // arcs per lane per round group
 constexpr uint32_t NEAR_STAGE = 4096;  // block staging capacity (near items)
+constexpr uint32_t SSSP_WARPS = 8;     // warps per block (256 threads)
+constexpr uint32_t NEAR_REGION = NEAR_STAGE / SSSP_WARPS;   // one region per warp
 constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
 
 // Where the appends of one processing segment go.
@@ -124,20 +126,26 @@ struct PushTargets {
 // block moves them to the global queues with one global atomicAdd each at
 // the end of the segment (flush_stage).  Full buffers spill straight to the
 // global queue.
+// The near buffer has one region per warp: a warp stages its own pushes
+// and, in the block-local rounds, relaxes them itself.
 struct Stage {
     uint32_t near_buf[NEAR_STAGE];
     uint32_t far_buf[FAR_STAGE];
-    uint32_t near_n, far_n, far_min;
+    uint32_t near_n[SSSP_WARPS];    // items staged per warp region
+    uint32_t local_lo[SSSP_WARPS];  // region[0, local_lo) was relaxed by its warp already
+    uint32_t near_off[SSSP_WARPS];  // flush: offset of each region's rest
+    uint32_t far_n, far_min;
     uint32_t base_near, base_far;
-    uint32_t local_lo;      // near_buf[0, local_lo) was relaxed by this block already
 };
 
 __device__ __forceinline__ void stage_reset(Stage &st) {
     if (threadIdx.x == 0) {
-        st.near_n = 0;
         st.far_n = 0;
         st.far_min = INF32;
-        st.local_lo = 0;
+    }
+    if (threadIdx.x < SSSP_WARPS) {
+        st.near_n[threadIdx.x] = 0;
+        st.local_lo[threadIdx.x] = 0;
     }
     __syncthreads();
 }
@@ -148,19 +156,27 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
 __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uint32_t n,
                                             uint32_t *err) {
     __syncthreads();
-    uint32_t lo = st.local_lo;
-    uint32_t nn = min(st.near_n, NEAR_STAGE), nf = min(st.far_n, FAR_STAGE);
-    nn = nn > lo ? nn - lo : 0;
+    const uint32_t nf = min(st.far_n, FAR_STAGE);
     if (threadIdx.x == 0) {
+        uint32_t nn = 0;
+        for (uint32_t w = 0; w < SSSP_WARPS; ++w) {
+            const uint32_t hi = min(st.near_n[w], NEAR_REGION), lo = st.local_lo[w];
+            st.near_off[w] = nn;
+            nn += hi > lo ? hi - lo : 0;
+        }
         st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
         st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
         if (st.far_min != INF32) atomicMin(t.far_min, st.far_min);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
-        uint32_t slot = st.base_near + i;
-        if (slot < n) t.qn[slot] = st.near_buf[lo + i];
-        else atomicOr(err, ERR_CAPACITY);
+    {   // each warp moves the rest of its own region
+        const uint32_t w = threadIdx.x >> 5;
+        const uint32_t hi = min(st.near_n[w], NEAR_REGION), lo = st.local_lo[w];
+        for (uint32_t i = lo + lane_id(); i < hi; i += 32) {
+            uint32_t slot = st.base_near + st.near_off[w] + (i - lo);
+            if (slot < n) t.qn[slot] = st.near_buf[w * NEAR_REGION + i];
+            else atomicOr(err, ERR_CAPACITY);
+        }
     }
     for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
         uint32_t slot = st.base_far + i;
@@ -174,8 +190,9 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
 __device__ __forceinline__ void push_near(const SsspArgs &a, Stage &st, const PushTargets &t,
                                           bool want, uint32_t v, uint32_t deg) {
     bool heavy = want && deg >= HEAVY_DEG;
-    stage_append(want && !heavy, v, st.near_buf, &st.near_n, NEAR_STAGE, t.qn, t.qn_count, a.n,
-                 &a.ctl->err);
+    const uint32_t w = threadIdx.x >> 5;
+    stage_append(want && !heavy, v, st.near_buf + w * NEAR_REGION, &st.near_n[w], NEAR_REGION, t.qn,
+                 t.qn_count, a.n, &a.ctl->err);
     if (heavy) {
         uint32_t nc = (deg + CHUNK - 1) / CHUNK;
         uint32_t base = atomicAdd(t.hqn_count, nc);
@@ -449,29 +466,28 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 }
             }
         }
-        // Block-local rounds: relax the vertices this block just staged for
-        // the next iteration right away, a hop further per round, instead
-        // of waiting for the grid barrier; what is left is flushed.  (A
-        // heavy-arc pass stages nothing near.)
+        // Local rounds: relax the vertices just staged for the next
+        // iteration right away, a hop further per round, instead of waiting
+        // for the grid barrier; what is left is flushed.  (A heavy-arc pass
+        // stages nothing near.)
         if (a.local_rounds && !hp) {
-            const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+            // Warp-local rounds: each warp relaxes the vertices it staged
+            // itself, a hop per round, with no block barrier between hops.
+            const uint32_t wib = threadIdx.x >> 5;
             const uint32_t tag_cur = t.tag_next - 1;
+            uint32_t *region = st.near_buf + wib * NEAR_REGION;
+            uint32_t lo = 0;
             for (uint32_t r = 0; r < a.local_rounds; ++r) {
-                __syncthreads();
-                const uint32_t lo = st.local_lo, hi = min(st.near_n, NEAR_STAGE);
-                __syncthreads();
+                __syncwarp();
+                const uint32_t hi = min(*(volatile uint32_t *)&st.near_n[wib], NEAR_REGION);
                 if (lo >= hi) break;
-                if (threadIdx.x == 0) st.local_lo = hi;
-                const uint32_t cnt = hi - lo;
-                const uint32_t lper = (cnt + nwb - 1) / nwb;
-                const uint32_t lbsz = lper <= 1 ? 1 : lper <= 2 ? 2 : lper <= 4 ? 4 : lper <= 8 ? 8 : lper <= 16 ? 16 : 32;
-                for (uint32_t b0 = wib * lbsz; b0 < cnt; b0 += nwb * lbsz) {
-                    uint32_t i = lo + b0 + lane;
-                    bool has = lane < lbsz && b0 + lane < cnt;
+                for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+                    const uint32_t i = b0 + lane;
+                    const bool has = i < hi;
                     uint32_t s = 0, deg = 0, u = 0, hdeg = 0;
                     uint64_t lab = INF64;
                     if (has) {
-                        u = st.near_buf[i];
+                        u = region[i];
                         // row offsets are read-only: issued before the exchange,
                         // they overlap it, and the arc loads then overlap the
                         // label load (one dependent round trip less per hop)
@@ -505,7 +521,9 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                                     attempts, improved);
                     }
                 }
+                lo = hi;
             }
+            if (lane == 0) st.local_lo[wib] = lo;
         }
         flush_stage(st, t, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
