@@ -541,6 +541,49 @@ def run_ablation_mode(args, world, rank, local):
                       "rows": rows}), flush=True)
 
 
+def run_weights_mode(args, world, rank, local):
+    """Sensitivity to the weight range (the paper's weight-range study):
+    R-MAT scale 22 with weights uniform in [1, w_max] for w_max from 100 to
+    100,000, one query of 64 seeds from the largest component; the Voronoi
+    phase at the autotuned band width and as a plain frontier, with
+    relaxations per arc."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import autotune
+    from paper_2205_14503_gb300 import steiner as st
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    rows = []
+    for wmax in (100, 1000, 10_000, 100_000):
+        g = wl.rmat(22, 16, (0.57, 0.19, 0.19), wmax, wl.CONFIG_SEED + 4, True)
+        seeds = wl.sample_distinct(wl.largest_cc(g), 64, wl.CONFIG_SEED + 4 + wmax)
+        with st.SteinerGraph(g, device=local) as G:
+            tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
+            row = {"w_max": wmax, "delta": tuned["delta"]}
+            ref = None
+            for name, delta in (("tuned", tuned["delta"]), ("frontier", 0x7FFFFFFF)):
+                G.set_param("delta", delta)
+                G.query_detail(seeds, pairs=False)
+                ms, att = [], []
+                for _ in range(max(1, args.steps)):
+                    r = G.query_detail(seeds, pairs=False)
+                    ms.append(r.stats["ms_voronoi"])
+                    att.append(r.stats["relax_attempts"] / g.n_arcs)
+                ref = r.total if ref is None else ref
+                assert r.total == ref, "schedules must reach the same tree"
+                row[f"{name}_ms"] = statistics.median(ms)
+                row[f"{name}_relaxations_per_arc"] = statistics.mean(att)
+            row["total"] = int(ref)
+            rows.append(row)
+        del g
+    print(json.dumps({"metric": "Voronoi time vs weight range (R-MAT 22, k = 64)", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,10 +605,12 @@ def main():
                     help="batch mode, profiling only: R-MAT scale instead of 22")
     ap.add_argument("--with-large", action="store_true",
                     help="ablation mode: include the R-MAT scale-26 workload")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation", "weights"],
+                    default="plain",
                     help="plain: the grid single-query workload (default); batch: R-MAT 22 with "
                          "64 batched queries; serve: R-MAT 24 query stream; ablation: "
-                         "relaxation order on the single-query workloads")
+                         "relaxation order on the single-query workloads; weights: "
+                         "sensitivity to the weight range")
     ap.add_argument("--queries", type=int, default=2000, help="serve mode: stream length")
     ap.add_argument("--plain-sample", type=int, default=200,
                     help="serve mode: queries timed one at a time for the plain comparison")
@@ -580,6 +625,8 @@ def main():
             run_serve_mode(args, world, rank, local)
         elif args.mode == "ablation":
             run_ablation_mode(args, world, rank, local)
+        elif args.mode == "weights":
+            run_weights_mode(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:
