@@ -421,73 +421,80 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                 const bool hv = idx >= n_items;        // heavy-arc pass item
                 const uint64_t wend = i0 + 32 < n_all ? gpre(i0 + 32) : W;
                 const uint64_t stop = min(p1, wend);
-                const uint64_t pbase = __shfl_sync(FULL, pre, 0);
-                // window-relative prefixes fit 32 bits (an item has at most
-                // deg x 64 pairs)
-                const uint32_t rel = idx < n_all ? (uint32_t)(pre - pbase) : 0xFFFFFFFFu;
-                // pair index -> (arc j, slot t) = divmod(local, c): multiply by
-                // ceil(2^40 / c), exact for local < 2^32 and c <= 64
-                const uint64_t mag = st.mag[c];
-                for (; p < stop; p += 32 * MQ_ILP) {
-                    bool valid[MQ_ILP], heavy[MQ_ILP];
-                    uint32_t arc[MQ_ILP], qs[MQ_ILP];
-                    uint64_t labs[MQ_ILP];
-                    const uint64_t plast = min(p + 32 * MQ_ILP, stop) - 1;
-                    const uint32_t ow0 = warp_owner_search(rel, (uint32_t)(p - pbase));
-                    const uint32_t owl = warp_owner_search(rel, (uint32_t)(plast - pbase));
-                    if (ow0 == owl) {
-                        // the whole round lies in one item (dense masks, long
-                        // rows): its fields once, no per-pair owner search
-                        const uint32_t ro = __shfl_sync(FULL, rel, ow0);
-                        const uint32_t so = __shfl_sync(FULL, s0, ow0);
-                        const uint32_t uo = __shfl_sync(FULL, u, ow0);
-                        const uint32_t co = __shfl_sync(FULL, c, ow0);
-                        const unsigned long long Mo = __shfl_sync(FULL, M, ow0);
-                        const uint64_t mo = __shfl_sync(FULL, mag, ow0);
-                        const bool ho = __shfl_sync(FULL, hv, ow0);
+                // The window's items one after another: an item's pairs are
+                // (arc j, slot t) -> j * c + t; the lanes take fixed slots
+                // (and, for c <= 16, several arcs per step), so a lane finds
+                // its slot and loads the tail's label once per item and then
+                // steps over the arcs with one broadcast arc load per arc.
+                for (uint32_t w = 0; w < 32; ++w) {
+                    const uint64_t pre_w = __shfl_sync(FULL, pre, w);
+                    if (pre_w >= stop) break;
+                    uint64_t end_w = w < 31 ? __shfl_sync(FULL, pre, w + 1) : wend;
+                    end_w = min(end_w, stop);
+                    const uint32_t cw = __shfl_sync(FULL, c, w);
+                    if (cw == 0 || end_w <= p || end_w <= pre_w) continue;
+                    const uint32_t uw = __shfl_sync(FULL, u, w);
+                    const uint32_t sw = __shfl_sync(FULL, s0, w);
+                    const unsigned long long Mw = __shfl_sync(FULL, M, w);
+                    const bool hw = __shfl_sync(FULL, hv, w);
+                    // the item's pairs inside this chunk: [lo, hi)
+                    const uint32_t lo = (uint32_t)((p > pre_w ? p : pre_w) - pre_w);
+                    const uint32_t hi = (uint32_t)(end_w - pre_w);
+                    const uint64_t mw = st.mag[cw];
+                    const uint32_t jlo = cw > 1 ? (uint32_t)__umul64hi((uint64_t)lo, mw << 24) : lo;
+                    const uint32_t jhi = cw > 1 ? (uint32_t)__umul64hi((uint64_t)(hi - 1), mw << 24) : hi - 1;
+                    if (cw <= 32) {
+                        // g lanes per arc (g = c rounded up to a power of two),
+                        // 32 / g arcs per step
+                        const uint32_t gsh = cw <= 1 ? 0u : 32u - __clz(cw - 1);
+                        const uint32_t A = 32u >> gsh;
+                        const uint32_t tq = lane & ((1u << gsh) - 1u), aoff = lane >> gsh;
+                        const bool tok = tq < cw;
+                        const uint32_t q = tok ? nth_bit64(Mw, tq) : 0u;
+                        const uint64_t lab = tok ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q]) : INF64;
+                        for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP * A) {
+                            bool valid[MQ_ILP], heavy[MQ_ILP];
+                            uint32_t arc[MQ_ILP], qs[MQ_ILP];
+                            uint64_t labs[MQ_ILP];
 #pragma unroll
-                        for (int k = 0; k < MQ_ILP; ++k) {
-                            const uint64_t pp = p + lane + 32 * k;
-                            valid[k] = pp < stop;
-                            heavy[k] = ho;
-                            const uint32_t local = valid[k] ? (uint32_t)(pp - pbase) - ro : 0;
-                            uint32_t j = local, tq = 0;
-                            if (co > 1) {
-                                j = (uint32_t)__umul64hi((uint64_t)local, mo << 24);
-                                tq = local - j * co;
+                            for (int k = 0; k < MQ_ILP; ++k) {
+                                const uint32_t jj = j0 + (uint32_t)k * A + aoff;
+                                const uint32_t l = jj * cw + tq;
+                                valid[k] = tok && jj <= jhi && l >= lo && l < hi;
+                                heavy[k] = hw;
+                                arc[k] = sw + jj;
+                                qs[k] = q;
+                                labs[k] = lab;
                             }
-                            const uint32_t q = co == MQ_SLOTS ? tq : nth_bit64(Mo, tq);
-                            qs[k] = q;
-                            arc[k] = so + j;
-                            labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
+                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
                         }
                     } else {
+                        // 33..64 slots: each lane takes slots lane and lane + 32
+                        const uint32_t t1 = lane + 32;
+                        const bool tok1 = t1 < cw;
+                        const uint32_t q0 = cw == MQ_SLOTS ? lane : nth_bit64(Mw, lane);
+                        const uint32_t q1 = tok1 ? (cw == MQ_SLOTS ? t1 : nth_bit64(Mw, t1)) : 0u;
+                        const uint64_t lab0 = ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q0]);
+                        const uint64_t lab1 = tok1 ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q1]) : INF64;
+                        for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP / 2) {
+                            bool valid[MQ_ILP], heavy[MQ_ILP];
+                            uint32_t arc[MQ_ILP], qs[MQ_ILP];
+                            uint64_t labs[MQ_ILP];
 #pragma unroll
-                        for (int k = 0; k < MQ_ILP; ++k) {
-                            const uint64_t pp = p + lane + 32 * k;
-                            valid[k] = pp < stop;
-                            const uint32_t pr = valid[k] ? (uint32_t)(pp - pbase) : 0;
-                            const uint32_t owner = warp_owner_search(rel, pr);
-                            const uint32_t ro = __shfl_sync(FULL, rel, owner);
-                            const uint32_t so = __shfl_sync(FULL, s0, owner);
-                            const uint32_t uo = __shfl_sync(FULL, u, owner);
-                            const uint32_t co = __shfl_sync(FULL, c, owner);
-                            const unsigned long long Mo = __shfl_sync(FULL, M, owner);
-                            const uint64_t mo = __shfl_sync(FULL, mag, owner);
-                            heavy[k] = __shfl_sync(FULL, hv, owner);
-                            const uint32_t local = pr - ro;
-                            uint32_t j = local, tq = 0;
-                            if (valid[k] && co > 1) {        // several slots: split the index
-                                j = (uint32_t)__umul64hi((uint64_t)local, mo << 24);
-                                tq = local - j * co;
+                            for (int k = 0; k < MQ_ILP; ++k) {
+                                const uint32_t jj = j0 + (uint32_t)(k >> 1);
+                                const bool second = k & 1;
+                                const uint32_t tq = second ? t1 : lane;
+                                const uint32_t l = jj * cw + tq;
+                                valid[k] = (second ? tok1 : true) && jj <= jhi && l >= lo && l < hi;
+                                heavy[k] = hw;
+                                arc[k] = sw + jj;
+                                qs[k] = second ? q1 : q0;
+                                labs[k] = second ? lab1 : lab0;
                             }
-                            const uint32_t q = co == MQ_SLOTS ? tq : nth_bit64(Mo, tq);
-                            qs[k] = q;
-                            arc[k] = so + j;
-                            labs[k] = valid[k] ? ldcg_u64(&a.label[(uint64_t)uo * MQ_SLOTS + q]) : INF64;
+                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
                         }
                     }
-                    mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
                 }
                 p = stop;
                 i0 += 32;
