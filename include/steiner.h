@@ -114,7 +114,10 @@ typedef struct {
  * result (tree edges, pair arcs, cell/dist/pred) is still in the caller's
  * vertex ids and arc indices, and the tie rules use the caller's order.
  * The environment variable STEINER_RELABEL=0 or 1, read here, forces this
- * internal order off or on.
+ * internal order off or on; STEINER_DELTA=<n> sets the initial band width
+ * (default 32 x mean weight / mean degree; "delta" below changes it later).
+ * With STEINER_TRACE set, each single query prints its Voronoi loop's exit
+ * reason and its first iterations' frontier sizes to stderr.
  * Errors: STEINER_EINVAL (malformed graph or n_arcs >= 2^32),
  * STEINER_ENOMEM, STEINER_ECUDA.  Cites: Table "preliminaries_notation"
  * (positive integer distances); Section "Evaluation" (symmetric arcs).
