@@ -584,6 +584,49 @@ def run_weights_mode(args, world, rank, local):
                       "rows": rows}), flush=True)
 
 
+def run_seeds_mode(args, world, rank, local):
+    """Seed-selection strategies (the paper's seed-selection study): R-MAT
+    scale 20, k = 100 seeds chosen uniformly, by BFS levels, eccentric and
+    proximate (k-BFS); per strategy the device time, D and |E_S|, each tree
+    checked against the oracle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2205_14503_gb300.workloads as wl
+    from paper_2205_14503_gb300 import autotune
+    from paper_2205_14503_gb300 import steiner as st
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    g = wl.rmat(20, 16, (0.57, 0.19, 0.19), 1000, wl.CONFIG_SEED + 6, True)
+    pool = wl.largest_cc(g)
+    k, sd = 100, wl.CONFIG_SEED + 6
+    sets = {"uniform": wl.sample_distinct(pool, k, sd),
+            "bfs_level": wl.seeds_bfs_level(g, pool, k, sd),
+            "eccentric": wl.seeds_eccentric(g, pool, k, sd),
+            "proximate": wl.seeds_proximate(g, pool, k, sd)}
+    rows = []
+    with st.SteinerGraph(g, device=local) as G:
+        autotune.tune(G, g, [sets["uniform"]], cache_path=None, device=local)
+        for name, seeds in sets.items():
+            G.query_detail(seeds, pairs=False)
+            ms = []
+            for _ in range(max(1, args.steps)):
+                r = G.query_detail(seeds, pairs=False)
+                ms.append(sum(r.stats[x] for x in ("ms_init", "ms_voronoi", "ms_bridges",
+                                                   "ms_mst", "ms_tree")))
+            ref = oracle.steiner(g, seeds, want_labels=False)
+            rows.append({"strategy": name, "ms": statistics.median(ms),
+                         "ms_voronoi": r.stats["ms_voronoi"], "total_D": int(r.total),
+                         "tree_edges": int(r.edges.shape[0]),
+                         "matches_oracle": bool(ref.total == r.total
+                                                and np.array_equal(ref.edges, r.edges))})
+    print(json.dumps({"metric": "seed-selection strategies (R-MAT 20, k = 100)", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,12 +648,12 @@ def main():
                     help="batch mode, profiling only: R-MAT scale instead of 22")
     ap.add_argument("--with-large", action="store_true",
                     help="ablation mode: include the R-MAT scale-26 workload")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation", "weights"],
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation", "weights", "seeds"],
                     default="plain",
                     help="plain: the grid single-query workload (default); batch: R-MAT 22 with "
                          "64 batched queries; serve: R-MAT 24 query stream; ablation: "
                          "relaxation order on the single-query workloads; weights: "
-                         "sensitivity to the weight range")
+                         "sensitivity to the weight range; seeds: seed-selection strategies")
     ap.add_argument("--queries", type=int, default=2000, help="serve mode: stream length")
     ap.add_argument("--plain-sample", type=int, default=200,
                     help="serve mode: queries timed one at a time for the plain comparison")
@@ -627,6 +670,8 @@ def main():
             run_ablation_mode(args, world, rank, local)
         elif args.mode == "weights":
             run_weights_mode(args, world, rank, local)
+        elif args.mode == "seeds":
+            run_seeds_mode(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -65,6 +65,8 @@ def _load():
     lib.wl_abort.argtypes = [vp]
     lib.wl_components.restype = ctypes.c_int64
     lib.wl_components.argtypes = [u32, vp, vp, vp, i32, ctypes.POINTER(u64)]
+    lib.wl_bfs_levels.restype = ctypes.c_int64
+    lib.wl_bfs_levels.argtypes = [u32, vp, vp, u32, vp]
     _lib = lib
     return lib
 
@@ -231,6 +233,73 @@ def poisson_arrivals(q: int, rate: float, seed: int) -> np.ndarray:
     u = uniform01(seed, np.arange(q, dtype=np.uint64))
     gaps = -np.log1p(-u) / rate
     return np.cumsum(gaps)
+
+
+# ---------------------------------------------------------------------------
+# seed-selection variants (the paper's seed-selection study): uniform random
+# is sample_distinct over the largest component; the others are below
+# ---------------------------------------------------------------------------
+
+def bfs_levels(g: Graph, root: int) -> np.ndarray:
+    """Hop counts from ``root`` (int64; -1 where unreachable)."""
+    lvl = np.empty(g.n, dtype=np.uint32)
+    rc = _load().wl_bfs_levels(g.n, _ptr(g.row_ptr), _ptr(g.col), int(root), _ptr(lvl))
+    if rc < 0:
+        raise ValueError("bad BFS root")
+    out = lvl.astype(np.int64)
+    out[lvl == np.uint32(0xFFFFFFFF)] = -1
+    return out
+
+
+def seeds_bfs_level(g: Graph, pool: np.ndarray, k: int, seed: int) -> np.ndarray:
+    """k seeds spread over the BFS levels of a random root of ``pool`` (one
+    component): each level contributes in proportion to its size (largest
+    remainders), drawn uniformly within the level."""
+    pool = np.asarray(pool)
+    root = int(sample_distinct(pool, 1, seed)[0])
+    lvl = bfs_levels(g, root)[pool]
+    levels, counts = np.unique(lvl, return_counts=True)
+    quota = counts * k / counts.sum()
+    take = np.floor(quota).astype(np.int64)
+    rest = k - int(take.sum())
+    order = np.lexsort((levels, -(quota - take)))       # largest remainders, then lower level
+    take[order[:rest]] += 1
+    out = []
+    for i, (L, t) in enumerate(zip(levels.tolist(), take.tolist())):
+        if t:
+            out.append(sample_distinct(pool[lvl == L], t, seed + 1 + i))
+    return np.concatenate(out).astype(np.int32)
+
+
+def _k_bfs(g: Graph, pool: np.ndarray, k: int, seed: int, far: bool) -> np.ndarray:
+    pool = np.asarray(pool)
+    first = int(sample_distinct(pool, 1, seed)[0])
+    inside = np.zeros(g.n, dtype=bool)
+    inside[pool] = True
+    acc = np.zeros(g.n, dtype=np.int64)
+    chosen = [first]
+    taken = np.zeros(g.n, dtype=bool)
+    taken[first] = True
+    for _ in range(k - 1):
+        acc += bfs_levels(g, chosen[-1])
+        score = acc.astype(np.float64)
+        score[~inside | taken] = -np.inf if far else np.inf
+        nxt = int(np.argmax(score) if far else np.argmin(score))   # ties: smallest id
+        chosen.append(nxt)
+        taken[nxt] = True
+    return np.asarray(chosen, dtype=np.int32)
+
+
+def seeds_eccentric(g: Graph, pool: np.ndarray, k: int, seed: int) -> np.ndarray:
+    """k-BFS sources far apart: from a random first source, each next one is
+    the vertex of ``pool`` (one component) with the largest sum of BFS levels
+    from the sources chosen so far."""
+    return _k_bfs(g, pool, k, seed, far=True)
+
+
+def seeds_proximate(g: Graph, pool: np.ndarray, k: int, seed: int) -> np.ndarray:
+    """As seeds_eccentric with the smallest sum: seeds close together."""
+    return _k_bfs(g, pool, k, seed, far=False)
 
 
 # ---------------------------------------------------------------------------

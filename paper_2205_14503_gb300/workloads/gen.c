@@ -417,3 +417,34 @@ int64_t wl_components(uint32_t n, const uint32_t *row_ptr, const int32_t *col,
     *size = best;
     return rep;
 }
+
+/*
+ * Unweighted BFS levels from `root` (hop counts; UINT32_MAX where
+ * unreachable), for the seed-selection workload variants.  Returns the
+ * deepest level.
+ */
+int64_t wl_bfs_levels(uint32_t n, const uint32_t *row_ptr, const int32_t *col, uint32_t root,
+                      uint32_t *level) {
+    if (root >= n) return -1;
+    uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    if (!queue) return -2;
+    for (uint32_t v = 0; v < n; ++v) level[v] = UINT32_MAX;
+    uint64_t head = 0, tail = 0;
+    level[root] = 0;
+    queue[tail++] = root;
+    uint32_t deepest = 0;
+    while (head < tail) {
+        uint32_t u = queue[head++];
+        uint32_t lu = level[u];
+        if (lu > deepest) deepest = lu;
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            uint32_t v = (uint32_t)col[e];
+            if (level[v] == UINT32_MAX) {
+                level[v] = lu + 1;
+                queue[tail++] = v;
+            }
+        }
+    }
+    free(queue);
+    return deepest;
+}
