@@ -196,9 +196,9 @@ int steiner_serve_stop(steiner_graph_t g);
  *   "delta"        near/far band width of the Voronoi phase (>= 1)
  *   "sssp_blocks"  blocks of the persistent Voronoi kernel (0 = every
  *                  co-resident block; at most "sssp_max_blocks")
- *   "local_rounds" block-local relaxation rounds per frontier iteration
- *                  (0 = off): a block keeps relaxing the vertices it just
- *                  queued, a hop per round, before the grid barrier
+ *   "local_rounds" local relaxation rounds per frontier iteration
+ *                  (0 = off): each warp keeps relaxing the vertices it
+ *                  just queued, a hop per round, before the grid barrier
  *   "batch_delta"  band width of the multi-query engine (0 = w_max / 8 when
  *                  "delta" is at most the largest weight w_max, else "delta")
  *   "batch_yield_div"  a serving launch returns to the host (to retire and

@@ -1,13 +1,14 @@
 """Autotuner for the Voronoi (SSSP) phase.
 
 The near/far band width ``delta``, the persistent kernel's grid size and
-the number of block-local relaxation rounds per iteration trade iterations
-against wasted relaxations and barrier cost (a delta at or below the largest
-weight also switches on the light/heavy arc split, which cuts repeated
-relaxations of hub rows), and the best point depends on the graph: a high-diameter grid is latency-bound (block-local rounds carry
-the wavefront several hops per grid barrier), a scale-free graph is
-throughput-bound (no local rounds, all co-resident blocks, a band near the
-default).  ``tune`` tries a small grid of both on sample queries, timing
+the number of local relaxation rounds per iteration trade iterations
+against wasted relaxations and barrier cost (a delta at or below the
+largest weight also switches on the light/heavy arc split, which cuts
+repeated relaxations of hub rows), and the best point depends on the
+graph: a high-diameter grid is latency-bound (local rounds carry the
+wavefront several hops per grid barrier), a scale-free graph is
+throughput-bound (no local rounds, all co-resident blocks, a narrow band
+with the split on).  ``tune`` tries a small grid of both on sample queries, timing
 the Voronoi kernel with the library's own CUDA events, applies the fastest
 and caches it in a JSON file keyed by a fingerprint of the graph and the GPU
 name, so later handles of the same graph start tuned (``apply_cached``).
@@ -73,7 +74,7 @@ def apply_cached(G: "st.SteinerGraph", graph, cache_path: str = DEFAULT_CACHE,
 def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.125, 0.25, 0.5, 1, 2),
          block_fractions=(0.5, 1.0), local_rounds=(0, 32), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
-    """Times the Voronoi kernel over a grid of (delta, blocks, block-local
+    """Times the Voronoi kernel over a grid of (delta, blocks, local
     rounds) on the sample seed sets, applies the fastest and (optionally)
     caches it."""
     d0 = G.get_param("delta")

@@ -145,7 +145,7 @@ struct SsspParams {
     uint32_t max_iters;      // loop cap -> ERR_TIMEOUT
     uint32_t base_near;      // first near tag of this query
     uint32_t base_far;       // first far tag of this query
-    uint32_t local_rounds;   // block-local relaxation rounds per iteration
+    uint32_t local_rounds;   // warp-local relaxation rounds per iteration
     uint32_t base_band;      // first band-list tag of this query
 };
 

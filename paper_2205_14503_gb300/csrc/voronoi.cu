@@ -45,7 +45,7 @@ struct SsspArgs {
     uint32_t base_near;
     uint32_t base_far;
     uint32_t heavy_cap;
-    uint32_t local_rounds;   // block-local relaxation rounds per iteration (0 = off)
+    uint32_t local_rounds;   // warp-local relaxation rounds per iteration (0 = off)
     uint32_t *stamp_band;    // band-list membership tags
     uint32_t *band_q;        // vertices relaxed in the current band
     uint64_t *band_hq;       // heavy-row chunks of listed high-degree vertices
@@ -127,7 +127,7 @@ struct PushTargets {
 // the end of the segment (flush_stage).  Full buffers spill straight to the
 // global queue.
 // The near buffer has one region per warp: a warp stages its own pushes
-// and, in the block-local rounds, relaxes them itself.
+// and, in the local rounds, relaxes them itself.
 struct Stage {
     uint32_t near_buf[NEAR_STAGE];
     uint32_t far_buf[FAR_STAGE];
@@ -274,7 +274,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v];                           // independent of the exchange
             uint32_t r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
-            // with block-local rounds a staged vertex may be relaxed this very
+            // with local rounds a staged vertex may be relaxed this very
             // iteration: the stamp exchange releases the label (the local
             // reader acquire-exchanges the stamp, then reads the label)
             to_near[u] = (a.local_rounds ? exch_release(&a.stamp_near[v], t.tag_next)
