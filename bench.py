@@ -44,11 +44,19 @@ SSSP_SOURCES = ["paper_2205_14503_gb300/csrc/voronoi.cu", "paper_2205_14503_gb30
                 "paper_2205_14503_gb300/csrc/internal.h"]
 
 
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and with whitespace collapsed, so a
+    comment edit does not void a capture of the same code."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def sssp_source_hash() -> str:
     h = hashlib.sha256()
     for p in SSSP_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
