@@ -723,15 +723,14 @@ struct MqScanArgs {
     const uint32_t *orig_row_ptr;
 };
 
-// Arc `arc` of row v (which starts at rs) for slot q; bridge keys carry the
-// caller's arc index, as in the single-query scan.
-__device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, uint32_t v,
-                                             uint32_t rs, uint32_t arc, uint32_t q,
+// Arc `arc` = (v, e.x, e.y) of row v (which starts at rs) for slot q, with
+// the slot's labels lv of v and lu of e.x; bridge keys carry the caller's arc
+// index, as in the single-query scan.  A tight same-cell arc lowers pmin,
+// the lane's running minimum of v's pred arc.
+__device__ __forceinline__ void mq_scan_eval(const MqScanArgs &a, uint32_t v, uint32_t rs,
+                                             uint32_t arc, uint2 e, uint32_t q, uint64_t lv,
+                                             uint64_t lu, uint32_t &pmin,
                                              unsigned long long &overflow) {
-    if (!valid) return;
-    uint2 e = __ldg(&a.adj[arc]);
-    uint64_t lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)v * MQ_SLOTS + q]));
-    uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + q]));
     if (lv == INF64 || lu == INF64) {
         if (lv != lu) overflow |= 1ull << q;
         return;
@@ -739,7 +738,7 @@ __device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, ui
     uint32_t cv = (uint32_t)lv, cu = (uint32_t)lu;
     uint64_t dv = lv >> 32, du = lu >> 32;
     if (cu == cv) {
-        if (du + e.y == dv) atomicMin(&a.pred[(uint64_t)v * MQ_SLOTS + q], arc);
+        if (du + e.y == dv) pmin = min(pmin, arc);
     } else if (cv < cu) {
         uint64_t b = dv + e.y + du;
         if (b >= INF32) {
@@ -753,29 +752,80 @@ __device__ __forceinline__ void mq_scan_pair(const MqScanArgs &a, bool valid, ui
     }
 }
 
-// One vertex's arcs [s0, s1) for every slot of the launch.  Lanes are
-// grouped as in the SSSP kernel: a group of g lanes takes one arc, lane t of
-// the group the t-th slot (t + 32 on a second pass when over 32 slots).
+constexpr int SCAN_PAIR_ILP = 2;   // arcs in flight per lane in the slot-pair mode
+
+__device__ __forceinline__ void mq_store_pred(const MqScanArgs &a, uint32_t v, uint32_t q,
+                                              uint32_t pmin, bool whole_row) {
+    if (pmin == INF32) return;
+    uint32_t *pp = &a.pred[(uint64_t)v * MQ_SLOTS + q];
+    if (whole_row) *pp = pmin;
+    else atomicMin(pp, pmin);
+}
+
+// One vertex's arcs [s0, s1) for every slot of the launch.  Each lane keeps
+// its slots' labels of v and pred minima in registers and stores v's pred
+// once per slot (atomically when the row is split into chunks over several
+// warps).
+// Over 32 slots: lane l takes slots 2l and 2l + 1 (one 16-byte load of the
+// pair's labels per arc), and every lane walks every arc.
+// Otherwise lanes are grouped as in the SSSP kernel: a group of g lanes
+// takes one arc, lane t of the group the t-th slot; the groups' minima meet
+// by shuffles.
 __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uint32_t rs,
-                                            uint32_t s0, uint32_t s1, uint32_t cnt, uint32_t gsh,
-                                            unsigned long long &overflow) {
+                                            uint32_t s0, uint32_t s1, bool whole_row, uint32_t cnt,
+                                            uint32_t gsh, unsigned long long &overflow) {
     const uint32_t lane = lane_id();
-    const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh, tl = lane & (g - 1);
-    for (uint32_t pass = 0; pass * 32 < cnt; ++pass) {
-        const uint32_t ts = tl + pass * 32;
-        const bool has_slot = ts < cnt;
-        const uint32_t q = has_slot ? nth_bit64(a.slots, ts) : 0;
-        for (uint32_t j0 = s0; j0 < s1; j0 += apr * 4) {
+    if (cnt > 32) {
+        const uint32_t q0 = 2 * lane;
+        const bool h0 = (a.slots >> q0) & 1, h1 = (a.slots >> (q0 + 1)) & 1;
+        if (!h0 && !h1) return;
+        const ulonglong2 lv = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)v * MQ_SLOTS + q0]));
+        uint32_t p0 = INF32, p1 = INF32;
+        for (uint32_t j0 = s0; j0 < s1; j0 += SCAN_PAIR_ILP) {
+            uint2 e[SCAN_PAIR_ILP];
+            ulonglong2 lu[SCAN_PAIR_ILP];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t arc = j0 + k * apr + grp;
-                mq_scan_pair(a, has_slot && arc < s1, v, rs, arc, q, overflow);
+            for (int k = 0; k < SCAN_PAIR_ILP; ++k)
+                if (j0 + k < s1) e[k] = __ldg(&a.adj[j0 + k]);
+#pragma unroll
+            for (int k = 0; k < SCAN_PAIR_ILP; ++k)
+                if (j0 + k < s1)
+                    lu[k] = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)e[k].x * MQ_SLOTS + q0]));
+#pragma unroll
+            for (int k = 0; k < SCAN_PAIR_ILP; ++k) {
+                if (j0 + k >= s1) break;
+                if (h0) mq_scan_eval(a, v, rs, j0 + k, e[k], q0, lv.x, lu[k].x, p0, overflow);
+                if (h1) mq_scan_eval(a, v, rs, j0 + k, e[k], q0 + 1, lv.y, lu[k].y, p1, overflow);
+            }
+        }
+        if (h0) mq_store_pred(a, v, q0, p0, whole_row);
+        if (h1) mq_store_pred(a, v, q0 + 1, p1, whole_row);
+        return;
+    }
+    const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh, tl = lane & (g - 1);
+    const bool has_slot = tl < cnt;
+    const uint32_t q = has_slot ? nth_bit64(a.slots, tl) : 0;
+    const uint64_t lv = has_slot
+        ? __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)v * MQ_SLOTS + q]))
+        : INF64;
+    uint32_t pmin = INF32;
+    for (uint32_t j0 = s0; j0 < s1; j0 += apr * 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t arc = j0 + k * apr + grp;
+            if (has_slot && arc < s1) {
+                uint2 e = __ldg(&a.adj[arc]);
+                uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + q]));
+                mq_scan_eval(a, v, rs, arc, e, q, lv, lu, pmin, overflow);
             }
         }
     }
+    for (uint32_t off = g; off < 32; off <<= 1)
+        pmin = min(pmin, __shfl_xor_sync(FULL, pmin, off));
+    if (grp == 0 && has_slot) mq_store_pred(a, v, q, pmin, whole_row);
 }
 
-__global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
+__global__ void __launch_bounds__(256, 4) mq_scan_kernel(MqScanArgs a) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -791,7 +841,7 @@ __global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
             uint32_t rs = a.row_ptr[v];
             uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
-            mq_scan_row(a, v, rs, s, e, cnt, gsh, overflow);
+            mq_scan_row(a, v, rs, s, e, false, cnt, gsh, overflow);
         } else {
             uint32_t v0 = (wi - a.n_heavy_chunks) * 32;
             uint32_t vl = v0 + lane;
@@ -800,7 +850,7 @@ __global__ void __launch_bounds__(256) mq_scan_kernel(MqScanArgs a) {
             for (uint32_t l = 0; l < 32 && v0 + l < a.n; ++l) {
                 uint32_t s = __shfl_sync(FULL, rs, l), e = __shfl_sync(FULL, re, l);
                 if (e - s >= HEAVY_DEG) continue;          // covered by the chunk list
-                mq_scan_row(a, v0 + l, s, s, e, cnt, gsh, overflow);
+                mq_scan_row(a, v0 + l, s, s, e, true, cnt, gsh, overflow);
             }
         }
     }

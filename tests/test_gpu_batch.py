@@ -89,6 +89,21 @@ def test_batch_mixed_statuses_and_degenerate_queries():
             assert r.total == ref.total
 
 
+@pytest.mark.parametrize("nq", [1, 5, 17, 33, 47])
+def test_batch_scan_slot_layouts(nq):
+    """The batched pred + bridge scan takes slot pairs per lane above 32
+    slots and lane groups below; odd counts leave half pairs and idle lanes,
+    and the hub rows (degree >= 256) go through the chunked, atomic path."""
+    g = wl.rmat(13, 16, wmax=1000, seed=47)
+    assert np.diff(g.row_ptr).max() >= 256
+    pool = wl.largest_cc(g)
+    qs = _queries(pool, wl.log_uniform_sizes(nq, 2, 150, 10 + nq), 5 + nq)
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+    assert rc == st.STEINER_OK
+    _check(g, qs, res)
+
+
 def test_batch_unit_weights_ties():
     g = wl.rmat(12, 16, wmax=1, seed=44)
     pool = wl.largest_cc(g)
