@@ -39,11 +39,12 @@ struct ScanArgs {
     const uint32_t *orig_row_ptr;
 };
 
-// Arc `arc` of row v (which starts at rs).  The bridge key carries the
-// caller's arc index, so ties between equal bridges break on the caller's
-// CSR order whatever the internal vertex order.
+// Arc `arc` of row v.  The bridge key carries the caller's arc index,
+// cbase + arc (cbase: the caller's row start of v minus v's internal row
+// start, taken once per row), so ties between equal bridges break on the
+// caller's CSR order whatever the internal vertex order.
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
-                                         uint32_t rs, uint32_t arc, bool &overflow) {
+                                         uint32_t cbase, uint32_t arc, bool &overflow) {
     if (!valid) return;
     uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
     uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[e.x]));
@@ -63,7 +64,7 @@ __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t
             overflow = true;
             return;
         }
-        uint64_t key = (b << 32) | caller_arc(a.orig_of, a.orig_row_ptr, v, rs, arc);
+        uint64_t key = (b << 32) | (uint32_t)(cbase + arc);
         uint64_t *slot = &a.pairtab[pair_slot(cv, cu, a.k)];
         if (key < ldcg_u64(slot))
             atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
@@ -85,17 +86,19 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
             uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
             uint64_t lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
+            uint32_t cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, rs);
             for (uint32_t b = s; b < e; b += 32)
-                scan_arc(a, b + lane < e, v, lv, rs, b + lane, overflow);
+                scan_arc(a, b + lane < e, v, lv, cbase, b + lane, overflow);
         } else {
             uint32_t v = (wi - a.n_heavy_chunks) * 32 + lane;
-            uint32_t s = 0, deg = 0;
+            uint32_t s = 0, deg = 0, cbase = 0;
             uint64_t lv = INF64;
             if (v < a.n) {
                 s = a.row_ptr[v];
                 deg = a.row_ptr[v + 1] - s;
                 if (deg >= HEAVY_DEG) deg = 0;          // covered by the chunk list
                 lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
+                if (deg) cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, s);
             }
             uint32_t incl = warp_inclusive_scan(deg);
             uint32_t excl = incl - deg;
@@ -107,8 +110,9 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
                 uint32_t so = __shfl_sync(FULL, s, owner);
                 uint32_t eo = __shfl_sync(FULL, excl, owner);
                 uint64_t lo = __shfl_sync(FULL, lv, owner);
+                uint32_t co = __shfl_sync(FULL, cbase, owner);
                 uint32_t vo = (wi - a.n_heavy_chunks) * 32 + owner;
-                scan_arc(a, valid, vo, lo, so, so + (j - eo), overflow);
+                scan_arc(a, valid, vo, lo, co, so + (j - eo), overflow);
             }
         }
     }

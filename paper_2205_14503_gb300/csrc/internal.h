@@ -47,10 +47,13 @@ inline const uint32_t *active_lend(const DevGraph &g, uint32_t delta) {
     return (delta <= g.max_w && g.adj_w && g.lend && g.part_delta == delta) ? g.lend : nullptr;
 }
 
-// Caller's arc index of internal arc `arc` of internal row v starting at rs.
-__device__ __forceinline__ uint32_t caller_arc(const uint32_t *orig_of, const uint32_t *orig_row_ptr,
-                                               uint32_t v, uint32_t rs, uint32_t arc) {
-    return orig_of ? orig_row_ptr[orig_of[v]] + (arc - rs) : arc;
+// Offset from internal to caller arc indices along internal row v (which
+// starts at rs): the caller's index of internal arc `arc` of the row is
+// caller_arc_base(...) + arc, modulo 2^32.
+__device__ __forceinline__ uint32_t caller_arc_base(const uint32_t *orig_of,
+                                                    const uint32_t *orig_row_ptr, uint32_t v,
+                                                    uint32_t rs) {
+    return orig_of ? orig_row_ptr[orig_of[v]] - rs : 0u;
 }
 
 __device__ __forceinline__ uint32_t caller_id(const uint32_t *orig_of, uint32_t v) {

@@ -723,64 +723,92 @@ struct MqScanArgs {
     const uint32_t *orig_row_ptr;
 };
 
-// Arc `arc` = (v, e.x, e.y) of row v (which starts at rs) for slot q, with
-// the slot's labels lv of v and lu of e.x; bridge keys carry the caller's arc
-// index, as in the single-query scan.  A tight same-cell arc lowers pmin,
-// the lane's running minimum of v's pred arc.
-__device__ __forceinline__ void mq_scan_eval(const MqScanArgs &a, uint32_t v, uint32_t rs,
-                                             uint32_t arc, uint2 e, uint32_t q, uint64_t lv,
-                                             uint64_t lu, uint32_t &pmin,
-                                             unsigned long long &overflow) {
-    if (lv == INF64 || lu == INF64) {
-        if (lv != lu) overflow |= 1ull << q;
+// One slot's view of the row being scanned, held by the lane that serves
+// the slot: v's label, and the slot's pair table from the first entry of
+// v's cell's row of the upper triangle (pair_slot(cv, cv + 1, k)), so that
+// the entry of pair (cv, cu) is tab[cu - cv - 1].
+struct ScanSlot {
+    uint64_t lv;
+    uint64_t *tab;
+    uint32_t pmin;      // running minimum of v's pred arc
+    uint32_t q;
+};
+
+__device__ __forceinline__ ScanSlot mq_row_slot(const MqScanArgs &a, uint32_t v, uint32_t q,
+                                                uint64_t *tab, uint32_t k, uint64_t lv) {
+    ScanSlot r;
+    r.lv = lv;
+    r.q = q;
+    r.pmin = INF32;
+    const uint32_t cv = (uint32_t)lv;
+    r.tab = lv == INF64 ? tab : tab + pair_slot(cv, cv + 1, k);
+    return r;
+}
+
+// Arc `arc` = (v, e.x, e.y) for one slot, with lu the slot's label of e.x
+// and cbase + arc the caller's index of the arc (bridge keys carry it, as in
+// the single-query scan).  A tight same-cell arc lowers r.pmin.
+__device__ __forceinline__ void mq_scan_eval(ScanSlot &r, uint32_t arc, uint2 e, uint64_t lu,
+                                             uint32_t cbase, unsigned long long &overflow) {
+    if (r.lv == INF64 || lu == INF64) {
+        if (r.lv != lu) overflow |= 1ull << r.q;
         return;
     }
-    uint32_t cv = (uint32_t)lv, cu = (uint32_t)lu;
-    uint64_t dv = lv >> 32, du = lu >> 32;
+    const uint32_t cv = (uint32_t)r.lv, cu = (uint32_t)lu;
+    const uint64_t dv = r.lv >> 32, du = lu >> 32;
     if (cu == cv) {
-        if (du + e.y == dv) pmin = min(pmin, arc);
+        if (du + e.y == dv) r.pmin = min(r.pmin, arc);
     } else if (cv < cu) {
         uint64_t b = dv + e.y + du;
         if (b >= INF32) {
-            overflow |= 1ull << q;
+            overflow |= 1ull << r.q;
             return;
         }
-        uint64_t key = (b << 32) | caller_arc(a.orig_of, a.orig_row_ptr, v, rs, arc);
-        uint64_t *slot = &a.pairtab[q][pair_slot(cv, cu, a.k[q])];
+        uint64_t key = (b << 32) | (uint32_t)(cbase + arc);
+        uint64_t *slot = r.tab + (cu - cv - 1);
         if (key < ldcg_u64(slot))
             atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
     }
 }
 
-constexpr int SCAN_PAIR_ILP = 2;   // arcs in flight per lane in the slot-pair mode
-
-__device__ __forceinline__ void mq_store_pred(const MqScanArgs &a, uint32_t v, uint32_t q,
-                                              uint32_t pmin, bool whole_row) {
-    if (pmin == INF32) return;
-    uint32_t *pp = &a.pred[(uint64_t)v * MQ_SLOTS + q];
-    if (whole_row) *pp = pmin;
-    else atomicMin(pp, pmin);
+__device__ __forceinline__ void mq_store_pred(const MqScanArgs &a, uint32_t v, const ScanSlot &r,
+                                              bool whole_row) {
+    if (r.pmin == INF32) return;
+    uint32_t *pp = &a.pred[(uint64_t)v * MQ_SLOTS + r.q];
+    if (whole_row) *pp = r.pmin;
+    else atomicMin(pp, r.pmin);
 }
 
+constexpr int SCAN_PAIR_ILP = 2;   // arcs in flight per lane in the slot-pair mode
+
+// The slots a lane serves for the whole launch, with their pair tables and
+// sizes loaded once.
+struct LaneSlots {
+    uint32_t q0, k0, k1;
+    bool h0, h1;
+    uint64_t *t0, *t1;
+};
+
 // One vertex's arcs [s0, s1) for every slot of the launch.  Each lane keeps
-// its slots' labels of v and pred minima in registers and stores v's pred
-// once per slot (atomically when the row is split into chunks over several
-// warps).
+// its slots' row state in registers and stores v's pred once per slot
+// (atomically when the row is split into chunks over several warps).
 // Over 32 slots: lane l takes slots 2l and 2l + 1 (one 16-byte load of the
 // pair's labels per arc), and every lane walks every arc.
 // Otherwise lanes are grouped as in the SSSP kernel: a group of g lanes
 // takes one arc, lane t of the group the t-th slot; the groups' minima meet
 // by shuffles.
-__device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uint32_t rs,
-                                            uint32_t s0, uint32_t s1, bool whole_row, uint32_t cnt,
-                                            uint32_t gsh, unsigned long long &overflow) {
+__device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, const LaneSlots &ls, uint32_t v,
+                                            uint32_t rs, uint32_t s0, uint32_t s1, bool whole_row,
+                                            uint32_t cnt, uint32_t gsh,
+                                            unsigned long long &overflow) {
     const uint32_t lane = lane_id();
+    const uint32_t cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, rs);
+    const uint64_t *lrow = &a.label[(uint64_t)v * MQ_SLOTS];
     if (cnt > 32) {
-        const uint32_t q0 = 2 * lane;
-        const bool h0 = (a.slots >> q0) & 1, h1 = (a.slots >> (q0 + 1)) & 1;
-        if (!h0 && !h1) return;
-        const ulonglong2 lv = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)v * MQ_SLOTS + q0]));
-        uint32_t p0 = INF32, p1 = INF32;
+        if (!ls.h0 && !ls.h1) return;
+        const ulonglong2 lv = __ldg(reinterpret_cast<const ulonglong2 *>(&lrow[ls.q0]));
+        ScanSlot r0 = mq_row_slot(a, v, ls.q0, ls.t0, ls.k0, lv.x);
+        ScanSlot r1 = mq_row_slot(a, v, ls.q0 + 1, ls.t1, ls.k1, lv.y);
         for (uint32_t j0 = s0; j0 < s1; j0 += SCAN_PAIR_ILP) {
             uint2 e[SCAN_PAIR_ILP];
             ulonglong2 lu[SCAN_PAIR_ILP];
@@ -790,47 +818,60 @@ __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, uint32_t v, uin
 #pragma unroll
             for (int k = 0; k < SCAN_PAIR_ILP; ++k)
                 if (j0 + k < s1)
-                    lu[k] = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)e[k].x * MQ_SLOTS + q0]));
+                    lu[k] = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)e[k].x * MQ_SLOTS + ls.q0]));
 #pragma unroll
             for (int k = 0; k < SCAN_PAIR_ILP; ++k) {
                 if (j0 + k >= s1) break;
-                if (h0) mq_scan_eval(a, v, rs, j0 + k, e[k], q0, lv.x, lu[k].x, p0, overflow);
-                if (h1) mq_scan_eval(a, v, rs, j0 + k, e[k], q0 + 1, lv.y, lu[k].y, p1, overflow);
+                if (ls.h0) mq_scan_eval(r0, j0 + k, e[k], lu[k].x, cbase, overflow);
+                if (ls.h1) mq_scan_eval(r1, j0 + k, e[k], lu[k].y, cbase, overflow);
             }
         }
-        if (h0) mq_store_pred(a, v, q0, p0, whole_row);
-        if (h1) mq_store_pred(a, v, q0 + 1, p1, whole_row);
+        if (ls.h0) mq_store_pred(a, v, r0, whole_row);
+        if (ls.h1) mq_store_pred(a, v, r1, whole_row);
         return;
     }
-    const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh, tl = lane & (g - 1);
-    const bool has_slot = tl < cnt;
-    const uint32_t q = has_slot ? nth_bit64(a.slots, tl) : 0;
-    const uint64_t lv = has_slot
-        ? __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)v * MQ_SLOTS + q]))
-        : INF64;
-    uint32_t pmin = INF32;
+    const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh;
+    const bool has_slot = ls.h0;
+    ScanSlot r = mq_row_slot(a, v, ls.q0, ls.t0, ls.k0,
+                             has_slot ? __ldg(reinterpret_cast<const unsigned long long *>(&lrow[ls.q0]))
+                                      : INF64);
     for (uint32_t j0 = s0; j0 < s1; j0 += apr * 4) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t arc = j0 + k * apr + grp;
             if (has_slot && arc < s1) {
                 uint2 e = __ldg(&a.adj[arc]);
-                uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + q]));
-                mq_scan_eval(a, v, rs, arc, e, q, lv, lu, pmin, overflow);
+                uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + ls.q0]));
+                mq_scan_eval(r, arc, e, lu, cbase, overflow);
             }
         }
     }
     for (uint32_t off = g; off < 32; off <<= 1)
-        pmin = min(pmin, __shfl_xor_sync(FULL, pmin, off));
-    if (grp == 0 && has_slot) mq_store_pred(a, v, q, pmin, whole_row);
+        r.pmin = min(r.pmin, __shfl_xor_sync(FULL, r.pmin, off));
+    if (grp == 0 && has_slot) mq_store_pred(a, v, r, whole_row);
 }
 
-__global__ void __launch_bounds__(256, 4) mq_scan_kernel(MqScanArgs a) {
+__global__ void __launch_bounds__(256, 3) mq_scan_kernel(MqScanArgs a) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t cnt = (uint32_t)popc64(a.slots);
     const uint32_t gsh = cnt > 16 ? 5 : cnt > 8 ? 4 : cnt > 4 ? 3 : cnt > 2 ? 2 : cnt > 1 ? 1 : 0;
+    LaneSlots ls;
+    if (cnt > 32) {
+        ls.q0 = 2 * lane;
+        ls.h0 = (a.slots >> ls.q0) & 1;
+        ls.h1 = (a.slots >> (ls.q0 + 1)) & 1;
+    } else {
+        const uint32_t tl = lane & ((1u << gsh) - 1);
+        ls.h0 = tl < cnt;
+        ls.h1 = false;
+        ls.q0 = ls.h0 ? nth_bit64(a.slots, tl) : 0;
+    }
+    ls.t0 = ls.h0 ? a.pairtab[ls.q0] : nullptr;
+    ls.k0 = ls.h0 ? a.k[ls.q0] : 0;
+    ls.t1 = ls.h1 ? a.pairtab[ls.q0 + 1] : nullptr;
+    ls.k1 = ls.h1 ? a.k[ls.q0 + 1] : 0;
     const uint32_t n_batches = (a.n + 31) / 32;
     const uint32_t n_work = a.n_heavy_chunks + n_batches;
     unsigned long long overflow = 0;
@@ -841,7 +882,7 @@ __global__ void __launch_bounds__(256, 4) mq_scan_kernel(MqScanArgs a) {
             uint32_t rs = a.row_ptr[v];
             uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
-            mq_scan_row(a, v, rs, s, e, false, cnt, gsh, overflow);
+            mq_scan_row(a, ls, v, rs, s, e, false, cnt, gsh, overflow);
         } else {
             uint32_t v0 = (wi - a.n_heavy_chunks) * 32;
             uint32_t vl = v0 + lane;
@@ -850,7 +891,7 @@ __global__ void __launch_bounds__(256, 4) mq_scan_kernel(MqScanArgs a) {
             for (uint32_t l = 0; l < 32 && v0 + l < a.n; ++l) {
                 uint32_t s = __shfl_sync(FULL, rs, l), e = __shfl_sync(FULL, re, l);
                 if (e - s >= HEAVY_DEG) continue;          // covered by the chunk list
-                mq_scan_row(a, v0 + l, s, s, e, true, cnt, gsh, overflow);
+                mq_scan_row(a, ls, v0 + l, s, s, e, true, cnt, gsh, overflow);
             }
         }
     }
