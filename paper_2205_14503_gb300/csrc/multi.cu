@@ -260,35 +260,6 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
     }
 }
 
-// A lane's slots in a work item with c slots (mask M) at tail vertex u, and
-// the tail's labels for them: for c <= 32 lanes are grouped by c rounded up
-// to a power of two and lane t of a group takes the t-th slot (q1 unused);
-// for c > 32 lane l takes the l-th and (l + 32)-th slots.  Slots a lane does
-// not take get label INF.
-__device__ __forceinline__ void item_slots(const MqArgs &a, uint32_t c, unsigned long long M,
-                                           uint32_t u, uint32_t &q0, uint32_t &q1, uint64_t &lab0,
-                                           uint64_t &lab1) {
-    const uint32_t lane = lane_id();
-    const uint64_t *row = &a.label[(uint64_t)u * MQ_SLOTS];
-    q1 = 0;
-    lab1 = INF64;
-    if (c <= 32) {
-        const uint32_t gsh = c <= 1 ? 0u : 32u - __clz(c - 1);
-        const uint32_t tq = lane & ((1u << gsh) - 1u);
-        const bool tok = tq < c;
-        q0 = tok ? nth_bit64(M, tq) : 0u;
-        lab0 = tok ? ldcg_u64(&row[q0]) : INF64;
-    } else {
-        const uint32_t t1 = lane + 32;
-        q0 = c == MQ_SLOTS ? lane : nth_bit64(M, lane);
-        lab0 = ldcg_u64(&row[q0]);
-        if (t1 < c) {
-            q1 = c == MQ_SLOTS ? t1 : nth_bit64(M, t1);
-            lab1 = ldcg_u64(&row[q1]);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
     __shared__ MqStage st;
     MqControl *ctl = a.ctl;
@@ -455,25 +426,16 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                 // (and, for c <= 16, several arcs per step), so a lane finds
                 // its slot and loads the tail's label once per item and then
                 // steps over the arcs with one broadcast arc load per arc.
-                // The tail labels of item w + 1 are loaded while item w is
-                // relaxed (a lane's slots in an item: see item_slots).
-                uint32_t nq0, nq1;
-                uint64_t nlab0, nlab1;
-                item_slots(a, __shfl_sync(FULL, c, 0), __shfl_sync(FULL, M, 0),
-                           __shfl_sync(FULL, u, 0), nq0, nq1, nlab0, nlab1);
                 for (uint32_t w = 0; w < 32; ++w) {
                     const uint64_t pre_w = __shfl_sync(FULL, pre, w);
                     if (pre_w >= stop) break;
-                    const uint32_t q_a = nq0, q_b = nq1;
-                    const uint64_t lab_a = nlab0, lab_b = nlab1;
-                    if (w < 31)
-                        item_slots(a, __shfl_sync(FULL, c, w + 1), __shfl_sync(FULL, M, w + 1),
-                                   __shfl_sync(FULL, u, w + 1), nq0, nq1, nlab0, nlab1);
                     uint64_t end_w = w < 31 ? __shfl_sync(FULL, pre, w + 1) : wend;
                     end_w = min(end_w, stop);
                     const uint32_t cw = __shfl_sync(FULL, c, w);
                     if (cw == 0 || end_w <= p || end_w <= pre_w) continue;
+                    const uint32_t uw = __shfl_sync(FULL, u, w);
                     const uint32_t sw = __shfl_sync(FULL, s0, w);
+                    const unsigned long long Mw = __shfl_sync(FULL, M, w);
                     const bool hw = __shfl_sync(FULL, hv, w);
                     // the item's pairs inside this chunk: [lo, hi)
                     const uint32_t lo = (uint32_t)((p > pre_w ? p : pre_w) - pre_w);
@@ -488,8 +450,8 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                         const uint32_t A = 32u >> gsh;
                         const uint32_t tq = lane & ((1u << gsh) - 1u), aoff = lane >> gsh;
                         const bool tok = tq < cw;
-                        const uint32_t q = q_a;
-                        const uint64_t lab = lab_a;
+                        const uint32_t q = tok ? nth_bit64(Mw, tq) : 0u;
+                        const uint64_t lab = tok ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q]) : INF64;
                         for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP * A) {
                             bool valid[MQ_ILP], heavy[MQ_ILP];
                             uint32_t arc[MQ_ILP], qs[MQ_ILP];
@@ -510,8 +472,10 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
                         // 33..64 slots: each lane takes slots lane and lane + 32
                         const uint32_t t1 = lane + 32;
                         const bool tok1 = t1 < cw;
-                        const uint32_t q0 = q_a, q1 = q_b;
-                        const uint64_t lab0 = lab_a, lab1 = lab_b;
+                        const uint32_t q0 = cw == MQ_SLOTS ? lane : nth_bit64(Mw, lane);
+                        const uint32_t q1 = tok1 ? (cw == MQ_SLOTS ? t1 : nth_bit64(Mw, t1)) : 0u;
+                        const uint64_t lab0 = ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q0]);
+                        const uint64_t lab1 = tok1 ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q1]) : INF64;
                         for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP / 2) {
                             bool valid[MQ_ILP], heavy[MQ_ILP];
                             uint32_t arc[MQ_ILP], qs[MQ_ILP];
