@@ -232,36 +232,21 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
     if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
     bool to_near[MQ_ILP], to_far[MQ_ILP];
     unsigned long long act = 0;
-    const uint32_t lane = lane_id();
 #pragma unroll
     for (int i = 0; i < MQ_ILP; ++i) {
         to_near[i] = to_far[i] = false;
-        if (!__any_sync(FULL, imp[i])) continue;
-        // Lanes that improved the same head vertex (for c > 16 slots all
-        // lanes of a step share one arc) set its slot bits with one atomic
-        // per word, issued by the group's first lane.
-        const uint32_t v = e[i].x, q = qs[i];
-        const bool nr = imp[i] && nd[i] < st.T[q], fr = imp[i] && !nr;
-        const uint32_t grp = __match_any_sync(FULL, imp[i] ? v : 0xFFFFFFFFu);
-        const unsigned long long nb = nr ? 1ull << q : 0ull, fb = fr ? 1ull << q : 0ull;
-        const unsigned long long nb_all =
-            ((unsigned long long)__reduce_or_sync(grp, (uint32_t)(nb >> 32)) << 32) |
-            __reduce_or_sync(grp, (uint32_t)nb);
-        const unsigned long long fb_all =
-            ((unsigned long long)__reduce_or_sync(grp, (uint32_t)(fb >> 32)) << 32) |
-            __reduce_or_sync(grp, (uint32_t)fb);
         if (!imp[i]) continue;
         ++improved;
-        if (fr) atomicMin(&st.fmin[q], (uint32_t)nd[i]);
-        if (lane != __ffs(grp) - 1) continue;
-        if (nb_all) {
-            atomicOr(&a.nmask[v], nb_all);
+        uint32_t v = e[i].x, q = qs[i];
+        unsigned long long bit = 1ull << q;
+        if (nd[i] < st.T[q]) {
+            atomicOr(&a.nmask[v], bit);
             to_near[i] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
-            act |= nb_all;
-        }
-        if (fb_all) {
-            unsigned long long fresh = fb_all & ~atomicOr(&a.fmask[v], fb_all);
-            for (; fresh; fresh &= fresh - 1) atomicAdd(&st.fpend[__ffsll(fresh) - 1], 1);
+            act |= bit;
+        } else {
+            unsigned long long old = atomicOr(&a.fmask[v], bit);
+            if (!(old & bit)) atomicAdd(&st.fpend[q], 1);
+            atomicMin(&st.fmin[q], (uint32_t)nd[i]);
             to_far[i] = atomicExch(&a.in_far[v], 1u) == 0;
         }
     }
