@@ -23,7 +23,11 @@
 
 namespace stn {
 
-constexpr int MQ_ILP = 4;
+// (arc, slot) pairs in flight per lane.  Two, at six 256-thread blocks per
+// SM (40 registers), beat four at four blocks (64 registers): the kernel is
+// bound by the latency of each item's chain of L2 round trips, so more
+// resident warps pay more than more pairs per warp.
+constexpr int MQ_ILP = 2;
 constexpr uint32_t MQ_NEAR_STAGE = 1024;
 constexpr uint32_t MQ_FAR_STAGE = 512;
 
@@ -229,7 +233,10 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
         }
     }
     // most rounds improve nothing: skip the append machinery then
-    if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
+    bool any_imp = false;
+#pragma unroll
+    for (int i = 0; i < MQ_ILP; ++i) any_imp |= imp[i];
+    if (!__any_sync(FULL, any_imp)) return;
     bool to_near[MQ_ILP], to_far[MQ_ILP];
     unsigned long long act = 0;
 #pragma unroll
@@ -260,7 +267,7 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
     }
 }
 
-__global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
+__global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
     __shared__ MqStage st;
     MqControl *ctl = a.ctl;
     const uint32_t lane = lane_id();
@@ -383,8 +390,8 @@ __global__ void __launch_bounds__(256, 4) mq_sssp_kernel(MqArgs a) {
         // shared by many warps.  Lane i finds the first item of the warp's
         // i-th chunk (all 32 searches at once).  Inside a chunk the warp
         // slides a window of 32 consecutive items (one per lane, loaded in
-        // parallel) and spreads the window's pairs over its lanes, 4 per lane
-        // in flight.
+        // parallel) and spreads the window's pairs over its lanes, MQ_ILP per
+        // lane in flight.
         const uint64_t W = st.W;
         auto gpre = [&](uint32_t i) -> uint64_t {
             return st.boff[i / seg] + __ldcg(reinterpret_cast<const unsigned long long *>(&a.item_pre[i]));
