@@ -858,7 +858,7 @@ __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, const LaneSlots
     if (grp == 0 && has_slot) mq_store_pred(a, v, r, whole_row);
 }
 
-__global__ void __launch_bounds__(256, 4) mq_scan_kernel(MqScanArgs a) {
+__global__ void __launch_bounds__(256, 5) mq_scan_kernel(MqScanArgs a) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
