@@ -97,7 +97,7 @@ struct BatchEngine {
     }
 
     void release() {
-        if (m.ctl) mq_free(m);
+        mq_free(m);                      // also after a partial mq_alloc
         if (doorbell_host) cudaFreeHost(doorbell_host);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (h_masks) cudaFreeHost(h_masks);
@@ -213,8 +213,9 @@ struct BatchEngine {
     // Runs the persistent kernel; returns the newly converged slots in
     // *done (slots stopped by an error are reported in *failed with *why).
     // yield: leave the kernel early (retire converged slots, admit waiting
-    // queries).  It leaves once an eighth of the in-flight slots converged,
-    // so the retirement scan is shared by several slots.
+    // queries): once popc(in flight) / yield_div slots converged (at least
+    // one; by default all of them, a whole wave), so that one retirement
+    // scan is shared by several slots, or when the doorbell rings.
     int run(bool yield, unsigned long long *done, unsigned long long *failed, int *why) {
         cudaStream_t s = api_stream(G);
         *done = *failed = 0;
