@@ -185,6 +185,10 @@ int steiner_query_batch(steiner_graph_t g, const int32_t *const *seeds, const ui
  * (seeds copied; non-blocking) and returns a ticket; steiner_poll returns
  * STEINER_PENDING until the result is ready, then fills *out once.
  * steiner_submit returns STEINER_EBUSY if the queue is full.
+ * steiner_submit and steiner_poll may be called from any thread while the
+ * loop runs.  steiner_serve_stop joins the loop's worker thread and frees
+ * the serving state (results not yet polled are dropped): it must not run
+ * concurrently with steiner_submit or steiner_poll on the same handle.
  */
 int steiner_serve_start(steiner_graph_t g, uint32_t slots, uint64_t budget_bytes);
 int steiner_submit(steiner_graph_t g, const int32_t *seeds, uint32_t k, uint64_t *ticket);

@@ -438,7 +438,7 @@ struct ServeEngine {
                     }
                     waiting.clear();
                 }
-                *B->doorbell_host = 0;
+                if (B->doorbell_host) *B->doorbell_host = 0;   // null after a failed set-up
                 // admit what fits; the rest goes back to the queue head
                 while (!waiting.empty()) {
                     uint32_t kq = (uint32_t)waiting.front().seeds.size();
@@ -548,10 +548,12 @@ int steiner_query_batch(steiner_graph_t G, const int32_t *const *seeds, const ui
 
 int steiner_serve_start(steiner_graph_t G, uint32_t slots, uint64_t budget_bytes) {
     if (!G) return STEINER_EINVAL;
+    // the graph mutex makes the check-and-create atomic; the worker's first
+    // pass waits on it until this call returns
+    std::lock_guard<std::mutex> glk(api_mutex(G));
     ServeEngine *&S = api_serve(G);
     if (S) return STEINER_OK;
     {
-        std::lock_guard<std::mutex> glk(api_mutex(G));
         BatchEngine *B = engine_of(G);
         int rc = B->init();
         if (rc) return rc;
