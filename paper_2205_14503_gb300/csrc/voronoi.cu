@@ -102,7 +102,8 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr,
 // relaxation: U arcs in flight per lane; frontier appends staged per block
 // ---------------------------------------------------------------------------
 
-constexpr int ILP = 4;                 // arcs per lane per round group
+constexpr int ILP = 4;                 // arcs per lane per round group (relax_group's
+                                       // early exit tests imp[0..3] by name: keep 4)
 constexpr uint32_t NEAR_STAGE = 4096;  // block staging capacity (near items)
 constexpr uint32_t SSSP_WARPS = 8;     // warps per block (256 threads)
 constexpr uint32_t NEAR_REGION = NEAR_STAGE / SSSP_WARPS;   // one region per warp
