@@ -183,8 +183,10 @@ int steiner_query_batch(steiner_graph_t g, const int32_t *const *seeds, const ui
  * `slots` concurrent query slots within `budget_bytes` of per-query device
  * state and starts the device loop; steiner_submit enqueues a query
  * (seeds copied; non-blocking) and returns a ticket; steiner_poll returns
- * STEINER_PENDING until the result is ready, then fills *out once.
- * steiner_submit returns STEINER_EBUSY if the queue is full.
+ * STEINER_PENDING until the result is ready, then fills *out once and
+ * returns the query's status.  Polling a ticket that was never issued, or
+ * whose result was already returned, gives STEINER_EINVAL and leaves *out
+ * untouched.  steiner_submit returns STEINER_EBUSY if the queue is full.
  * steiner_submit and steiner_poll may be called from any thread while the
  * loop runs.  steiner_serve_stop joins the loop's worker thread and frees
  * the serving state (results not yet polled are dropped): it must not run
@@ -214,8 +216,10 @@ int steiner_serve_stop(steiner_graph_t g);
  * "heavy_chunks" and the multi-query engine's tracing counters
  * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
  * microseconds, "batch_launches", "batch_iterations", "batch_items",
- * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds; "batch_reset"
- * clears the timers).  It returns -1 for an unknown key.
+ * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds, "batch_admitted"
+ * (queries admitted into slots) and "batch_admitted_busy" (of those, the
+ * ones admitted while other slots were still on the device); "batch_reset"
+ * clears the timers and counters).  It returns -1 for an unknown key.
  */
 int steiner_set_param(steiner_graph_t g, const char *key, int64_t value);
 int64_t steiner_get_param(steiner_graph_t g, const char *key);
@@ -230,7 +234,8 @@ int64_t steiner_get_param(steiner_graph_t g, const char *key);
  * present on every GPU that loads the library until the process exits.
  * The paper has no counterpart to this entry point.
  *   row_ptr, col, w  device, the CSR of the graph in the steiner_load_graph
- *                    format (not re-validated; neighbour ids are range-checked)
+ *                    format (row offsets and neighbour ids are range-checked;
+ *                    sortedness and symmetry are not re-validated)
  *   n, n_arcs        sizes; n <= STEINER_NOALLOC_MAX_VERTICES
  *   seeds            device, k distinct seed ids in ASCENDING order
  *   cell, dist, pred device outputs, n entries each (may be NULL), same
@@ -243,8 +248,10 @@ int64_t steiner_get_param(steiner_graph_t g, const char *key);
  * so calls that overlap on the GPU (other streams or host threads) race:
  * serialise them.  Errors: STEINER_ENOMEM if n exceeds the limit (nothing
  * is launched), STEINER_EINVAL (bad sizes, unsorted or out-of-range seeds,
- * out-of-range neighbour ids), STEINER_EOVERFLOW, STEINER_ETIMEOUT,
- * STEINER_ECUDA.
+ * row offsets that do not run from 0 to n_arcs without decreasing,
+ * out-of-range neighbour ids; the outputs are then left untouched),
+ * STEINER_EOVERFLOW, STEINER_ETIMEOUT, STEINER_ECUDA (after these three the
+ * outputs' contents are undefined).
  */
 #define STEINER_NOALLOC_MAX_VERTICES 1048576u
 int steiner_voronoi_noalloc(const uint32_t *row_ptr, const int32_t *col, const uint32_t *w,

@@ -279,9 +279,24 @@ int query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_res
     if (getenv("STEINER_TRACE")) {
         fprintf(stderr, "[steiner] err=0x%x exit=%u iterations=%u phases=%u attempts=%llu\n",
                 c.err, c.exit_reason, c.iterations, c.phases, c.relax_attempts);
-        for (int i = 0; i < TRACE_LEN && i < (int)c.iterations + 1; ++i)
-            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u\n", i, c.trace[i][0],
-                    c.trace[i][1], c.trace[i][2], c.trace[i][3]);
+        const int nt = std::min<int>(TRACE_LEN, (int)c.iterations);
+        for (int i = 0; i < nt; ++i) {
+            // a far-pile split takes an iteration index of its own and is
+            // not traced; its time counts with the iteration before it
+            if (!c.trace_ns[i]) {
+                fprintf(stderr, "[steiner]   it %d: far-pile split\n", i);
+                continue;
+            }
+            unsigned long long t1 = (int)c.iterations <= TRACE_LEN ? c.end_ns : 0;
+            for (int j = i + 1; j < nt; ++j)
+                if (c.trace_ns[j]) {
+                    t1 = c.trace_ns[j];
+                    break;
+                }
+            double us = t1 > c.trace_ns[i] ? 1e-3 * (double)(t1 - c.trace_ns[i]) : -1.0;
+            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u  %.1f us\n", i,
+                    c.trace[i][0], c.trace[i][1], c.trace[i][2], c.trace[i][3], us);
+        }
     }
     if (rc == STEINER_OK || rc == STEINER_EDISCONNECTED) {
         int rc2 = fetch_tree(G, out);

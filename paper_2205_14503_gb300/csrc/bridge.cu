@@ -256,7 +256,8 @@ cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs
     }
     uint64_t work = (uint64_t)g.n_heavy_chunks + (g.n + 31) / 32;
     uint64_t blocks = (work + 7) / 8;          // 8 warps per block
-    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    const uint64_t cap = (uint64_t)current_sm_count() * 32;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
     return cudaGetLastError();

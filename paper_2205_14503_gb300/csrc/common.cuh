@@ -90,6 +90,13 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, uint32_t *err) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// The GPU's global nanosecond timer (for the iteration trace).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Exchanges with release / acquire semantics at GPU scope.  A relaxation
 // that improves a label then release-exchanges the vertex's queue stamp; a
 // block taking the vertex from its staging buffer acquire-exchanges the

@@ -2,9 +2,30 @@
 // symmetric with positive integer weights: Table "preliminaries_notation",
 // Section "Evaluation") and interleaving of (neighbour, weight) into one
 // 8-byte record per arc, so a relaxation reads one sector-aligned pair.
+#include <atomic>
+
 #include "internal.h"
 
 namespace stn {
+
+int current_sm_count() {
+    constexpr int MAX_DEVICES = 64;
+    static std::atomic<int> cache[MAX_DEVICES];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    int sms = dev >= 0 ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (sms > 0) return sms;
+    if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
 
 enum : uint32_t {
     BAD_RANGE = 1u,      // neighbour id out of range
@@ -114,7 +135,8 @@ __global__ void __launch_bounds__(256) partition_kernel(const uint32_t *__restri
 
 cudaError_t launch_partition(const DevGraph &g, uint32_t delta, cudaStream_t s) {
     uint64_t blocks = ((uint64_t)g.n + 7) / 8;
-    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    const uint64_t cap = (uint64_t)current_sm_count() * 32;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     partition_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.n, delta, g.adj_w, g.lend);
     return cudaGetLastError();
@@ -141,7 +163,8 @@ cudaError_t launch_validate_graph(const uint32_t *row_ptr, const int32_t *col, c
                                   cudaStream_t s) {
     (void)m;
     uint64_t blocks = ((uint64_t)n + 255) / 256;
-    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    const uint64_t cap = (uint64_t)current_sm_count() * 16;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     validate_kernel<<<(unsigned)blocks, 256, 0, s>>>(row_ptr, col, w, n, adj, new_of, new_row_ptr,
                                                       bad, max_w);

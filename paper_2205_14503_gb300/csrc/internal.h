@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t internal_id(const uint32_t *new_of, uint32_t
     return new_of ? new_of[v] : v;
 }
 
-constexpr int TRACE_LEN = 64;
+constexpr int TRACE_LEN = 128;
 
 // Device control block of one query.
 struct Control {
@@ -93,6 +93,8 @@ struct Control {
     uint32_t band_hcount;
     uint32_t bands;
     uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
+    unsigned long long trace_ns[TRACE_LEN];   // their start times (global timer, ns)
+    unsigned long long end_ns;                // end of the last iteration
 };
 
 // Per-query device workspace for the single-query path.
@@ -151,6 +153,10 @@ struct SsspParams {
     uint32_t local_rounds;   // warp-local relaxation rounds per iteration
     uint32_t base_band;      // first band-list tag of this query
 };
+
+// SM count of the current device (queried once per device, then cached);
+// the launchers size their grids in multiples of it.
+int current_sm_count();
 
 // voronoi.cu
 cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t delta,

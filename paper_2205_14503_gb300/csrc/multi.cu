@@ -982,9 +982,9 @@ cudaError_t mq_launch_clear(const DevGraph &g, MqState &m, unsigned long long ma
                             cudaStream_t s) {
     if (!mask) return cudaSuccess;
     if (__builtin_popcountll(mask) >= 8) {
-        mq_clear_rows_kernel<<<152 * 16, 256, 0, s>>>(g.n, m.label, m.pred, mask);
+        mq_clear_rows_kernel<<<current_sm_count() * 16, 256, 0, s>>>(g.n, m.label, m.pred, mask);
     } else {
-        unsigned grid = (unsigned)std::min<uint64_t>((g.n + 255) / 256, 152ull * 16);
+        unsigned grid = (unsigned)std::min<uint64_t>((g.n + 255) / 256, (uint64_t)current_sm_count() * 16);
         for (unsigned long long mm = mask; mm; mm &= mm - 1)
             mq_clear_column_kernel<<<grid, 256, 0, s>>>(g.n, m.label, m.pred,
                                                         (uint32_t)__builtin_ctzll(mm));
@@ -1057,7 +1057,7 @@ cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slo
     a.orig_of = g.orig_of;
     a.orig_row_ptr = g.orig_row_ptr;
     uint64_t work = (uint64_t)g.n_heavy_chunks + (g.n + 31) / 32;
-    uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + 7) / 8, 152ull * 32));
+    uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + 7) / 8, (uint64_t)current_sm_count() * 32));
     mq_scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

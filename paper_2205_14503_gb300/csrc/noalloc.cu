@@ -41,7 +41,7 @@ struct NaControl {
     uint32_t iterations;
 };
 
-constexpr uint32_t NA_BAD_INPUT = 1u << 8;   // seed list or arc out of range
+constexpr uint32_t NA_BAD_INPUT = 1u << 8;   // seed list, row offsets or arc out of range
 
 // Layout of the scratch array: control block, then per-vertex arrays.
 constexpr size_t CTL_BYTES = 256;
@@ -60,6 +60,7 @@ struct NaArgs {
     const int32_t *col;
     const uint32_t *w;
     uint32_t n;
+    uint64_t n_arcs;
     const int32_t *seeds;
     uint32_t k;
     unsigned char *scratch;     // device address of g_scratch
@@ -82,23 +83,33 @@ __device__ __forceinline__ uint32_t *queue_of(const NaArgs &a, uint32_t it) {
     return reinterpret_cast<uint32_t *>(a.scratch + ((it & 1) ? Q1_OFF : Q0_OFF));
 }
 
-// Clears the control block and the per-vertex state of the previous call.
+// Clears the control block of the previous call (one thread).
+__global__ void na_ctl_reset_kernel(NaArgs a) {
+    NaControl *c = ctl_of(a);
+    c->bar.count = 0;
+    c->bar.gen = 0;
+    c->err = 0;
+    c->count[0] = c->count[1] = c->count[2] = 0;
+    c->iterations = 0;
+}
+
+// Clears the per-vertex state of the previous call and checks the row
+// offsets (row_ptr[0] = 0, non-decreasing, row_ptr[n] = n_arcs), so that no
+// later kernel reads an arc outside [0, n_arcs).
 __global__ void na_reset_kernel(NaArgs a) {
     uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid == 0) {
-        NaControl *c = ctl_of(a);
-        c->bar.count = 0;
-        c->bar.gen = 0;
-        c->err = 0;
-        c->count[0] = c->count[1] = c->count[2] = 0;
-        c->iterations = 0;
-    }
+    NaControl *c = ctl_of(a);
+    if (tid == 0 && (a.row_ptr[0] != 0 || (uint64_t)a.row_ptr[a.n] != a.n_arcs))
+        atomicOr(&c->err, NA_BAD_INPUT);
     uint64_t *label = label_of(a);
     uint32_t *stamp = stamp_of(a);
+    bool bad = false;
     for (uint32_t v = tid; v < a.n; v += gridDim.x * blockDim.x) {
         label[v] = INF64;
         stamp[v] = 0;
+        bad |= a.row_ptr[v] > a.row_ptr[v + 1];
     }
+    if (bad) atomicOr(&c->err, NA_BAD_INPUT);
 }
 
 // Seeds (ascending, distinct, in range) at distance 0 on the first frontier.
@@ -128,7 +139,7 @@ __global__ void __launch_bounds__(256) na_sssp_kernel(NaArgs a) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const bool first = blockIdx.x == 0 && threadIdx.x == 0;
-    if (ldcg_u32(&c->err) & NA_BAD_INPUT) return;        // set by the seed kernel: all blocks agree
+    if (ldcg_u32(&c->err) & NA_BAD_INPUT) return;   // set by the reset or seed kernel: all blocks agree
     for (uint32_t it = 0;; ++it) {
         uint32_t nf = min(ldcg_u32(&c->count[it % 3]), a.n);
         if (first) c->count[(it + 2) % 3] = 0;
@@ -193,8 +204,10 @@ __global__ void __launch_bounds__(256) na_sssp_kernel(NaArgs a) {
 // pred(v) = smallest-id tight neighbour in v's cell; outputs in the
 // steiner_voronoi format.  A reached vertex next to an unreached one means
 // a distance did not fit below 2^32 - 1 (ERR_OVERFLOW).
+// A rejected input (NA_BAD_INPUT) leaves the caller's outputs untouched.
 __global__ void na_export_kernel(NaArgs a) {
     NaControl *c = ctl_of(a);
+    if (ldcg_u32(&c->err) & NA_BAD_INPUT) return;
     const uint64_t *label = label_of(a);
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
         uint64_t lv = label[v];
@@ -227,6 +240,7 @@ struct DeviceSetup {
     bool ready = false;
     unsigned char *scratch = nullptr;
     int blocks = 0;
+    int sms = 0;
 };
 constexpr int NA_MAX_DEVICES = 64;
 static DeviceSetup g_setup[NA_MAX_DEVICES];
@@ -251,6 +265,7 @@ static int setup_device(int dev, DeviceSetup &out, const char **why) {
         }
         s.scratch = static_cast<unsigned char *>(ptr);
         s.blocks = per_sm * sms;
+        s.sms = sms;
         s.ready = true;
     }
     out = s;
@@ -294,8 +309,9 @@ extern "C" int steiner_voronoi_noalloc(const uint32_t *row_ptr, const int32_t *c
         return rc;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    NaArgs a{row_ptr, col, w, n, seeds, k, su.scratch, 1u << 22, cell, dist, pred};
-    unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    NaArgs a{row_ptr, col, w, n, n_arcs, seeds, k, su.scratch, 1u << 22, cell, dist, pred};
+    unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)su.sms * 16);
+    na_ctl_reset_kernel<<<1, 1, 0, s>>>(a);
     na_reset_kernel<<<grid, 256, 0, s>>>(a);
     na_seed_kernel<<<(k + 255) / 256, 256, 0, s>>>(a);
     void *args[] = {&a};
@@ -316,7 +332,8 @@ extern "C" int steiner_voronoi_noalloc(const uint32_t *row_ptr, const int32_t *c
     }
     if (err & NA_BAD_INPUT) {
         api_set_error("steiner_voronoi_noalloc: seeds must be distinct, ascending and below n, "
-                      "and every neighbour id below n");
+                      "row_ptr must run from 0 to n_arcs without decreasing, and every "
+                      "neighbour id must be below n");
         return STEINER_EINVAL;
     }
     if (err & (ERR_BARRIER | ERR_TIMEOUT)) {

@@ -22,6 +22,7 @@
 #include <deque>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "engine.h"
@@ -70,6 +71,9 @@ struct BatchEngine {
     // cumulative wall time (ms) and counters, for tracing
     double ms_sssp = 0, ms_scan = 0, ms_tail = 0, ms_admit = 0;
     uint64_t launches = 0, relax_attempts = 0, iterations_run = 0;
+    // admissions, and those made while other slots were on the device
+    // (continuous batching: a query joins a running batch)
+    uint64_t admitted = 0, admitted_busy = 0;
     std::atomic<int> free_slots{MQ_SLOTS};
 
     int init() {
@@ -199,6 +203,8 @@ struct BatchEngine {
             api_set_error(std::string("admission: ") + cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? STEINER_ENOMEM : STEINER_ECUDA;
         }
+        ++admitted;
+        if (inflight & ~staged) ++admitted_busy;
         slots[q].busy = true;
         slots[q].tag = tag;
         slots[q].k = k;
@@ -325,8 +331,8 @@ void destroy_batch(BatchEngine *b) {
 
 // Tracing counters of the multi-query engine (steiner_get_param keys
 // "batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit",
-// "batch_launches", "batch_iterations", "batch_relax_attempts"; "batch_reset"
-// clears them).
+// "batch_launches", "batch_iterations", "batch_relax_attempts",
+// "batch_admitted", "batch_admitted_busy"; "batch_reset" clears them).
 
 int64_t batch_counter(BatchEngine *B, const char *key) {
     if (!B) return -1;
@@ -338,6 +344,8 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_launches") return (int64_t)B->launches;
     if (k == "batch_iterations") return (int64_t)B->iterations_run;
     if (k == "batch_relax_attempts") return (int64_t)B->relax_attempts;
+    if (k == "batch_admitted") return (int64_t)B->admitted;
+    if (k == "batch_admitted_busy") return (int64_t)B->admitted_busy;
     if (k == "batch_delta") return B->cur_delta();
     if (k == "batch_yield_div") return B->yield_div;
     if (k.rfind("batch_t", 0) == 0 && k.size() == 8 && B->h_ctl) return (int64_t)B->h_ctl->t_part[k[7] - '0'];
@@ -346,6 +354,7 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_reset") {
         B->ms_sssp = B->ms_scan = B->ms_tail = B->ms_admit = 0;
         B->launches = B->iterations_run = 0;
+        B->admitted = B->admitted_busy = 0;
         return 0;
     }
     return -1;
@@ -401,6 +410,9 @@ struct ServeEngine {
     std::condition_variable cv;
     std::deque<ServeJob> queue;
     std::unordered_map<uint64_t, steiner_result_t> done;
+    // tickets issued and not yet returned by steiner_poll (queued, on the
+    // device, or finished and waiting in `done`)
+    std::unordered_set<uint64_t> live;
     std::unordered_map<uint64_t, double> t_submit;
     uint64_t next_ticket = 1;
     uint32_t max_queue = 1u << 16;
@@ -586,6 +598,7 @@ int steiner_submit(steiner_graph_t G, const int32_t *seeds, uint32_t k, uint64_t
     if (S->queue.size() >= S->max_queue) return STEINER_EBUSY;
     uint64_t t = S->next_ticket++;
     *ticket = t;
+    S->live.insert(t);
     if (rc) {
         steiner_result_t r{};
         r.status = rc;
@@ -604,10 +617,14 @@ int steiner_poll(steiner_graph_t G, uint64_t ticket, steiner_result_t *out) {
     ServeEngine *S = api_serve(G);
     if (!S) return STEINER_EINVAL;
     std::lock_guard<std::mutex> lk(S->mu);
+    // a ticket that was never issued, or whose result was already returned,
+    // is unknown: STEINER_EINVAL with *out untouched
+    if (!S->live.count(ticket)) return STEINER_EINVAL;
     auto it = S->done.find(ticket);
-    if (it == S->done.end()) return ticket < S->next_ticket ? STEINER_PENDING : STEINER_EINVAL;
+    if (it == S->done.end()) return STEINER_PENDING;
     *out = it->second;
     S->done.erase(it);
+    S->live.erase(ticket);
     return out->status;
 }
 

@@ -333,7 +333,7 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
                         uint32_t n_bits, cudaStream_t s) {
     if (k < 2) return cudaSuccess;
     uint64_t slots = (uint64_t)k * (k - 1) / 2;
-    uint32_t blocks = (uint32_t)std::min<uint64_t>((2 * slots + 255) / 256, 152ull * 8);
+    uint32_t blocks = (uint32_t)std::min<uint64_t>((2 * slots + 255) / 256, (uint64_t)current_sm_count() * 8);
     expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.orig_of, g.new_of, g.orig_row_ptr,
                                          g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
                                          ws.pred_stride, ws.mark, tag, n_bits, ws.tree_key,

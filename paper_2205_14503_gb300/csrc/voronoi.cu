@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 ctl->trace[it][1] = n_heavy;
                 ctl->trace[it][2] = ldcg_u32(&ctl->far_count[phase & 1]);
                 ctl->trace[it][3] = (uint32_t)T;
+                ctl->trace_ns[it] = global_ns();
             }
         }
         stage_reset(st);
@@ -645,6 +646,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         ctl->iterations = it;
         ctl->phases = phase;
         ctl->bands = bands;
+        ctl->end_ns = global_ns();
     }
 }
 // ---------------------------------------------------------------------------
@@ -683,7 +685,8 @@ __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
 static int grid_for(uint64_t items, int threads) {
     uint64_t b = (items + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152ull * 16) b = 152ull * 16;
+    const uint64_t cap = (uint64_t)current_sm_count() * 16;
+    if (b > cap) b = cap;
     return (int)b;
 }
 

@@ -267,8 +267,12 @@ def steiner_submit(h: int, seeds) -> tuple[int, int]:
 
 def steiner_poll(h: int, ticket: int):
     r = steiner_result_t()
+    # steiner_poll writes *out only when it returns a result; the sentinel
+    # tells a pending or unknown ticket (no result: None) from a query that
+    # finished with an error status
+    r.status = STEINER_PENDING
     rc = load_library().steiner_poll(h, ticket, ctypes.byref(r))
-    if rc == STEINER_PENDING or rc == STEINER_EINVAL and not r.edges and r.status == 0:
+    if rc == STEINER_PENDING or r.status == STEINER_PENDING:
         return rc, None
     return rc, _take_result(r)
 

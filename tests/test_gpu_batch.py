@@ -142,8 +142,19 @@ def test_serving_stream_matches_alone():
                 if rc != st.STEINER_PENDING:
                     results[t] = r
             time.sleep(0.001)
+        # a result is handed out once: the ticket is unknown afterwards
+        rc_again, r_again = st.steiner_poll(h, tickets[0])
+        launches = st.steiner_get_param(h, "batch_launches")
+        admitted = st.steiner_get_param(h, "batch_admitted")
+        admitted_busy = st.steiner_get_param(h, "batch_admitted_busy")
         st.steiner_serve_stop(h)
         alone = [Gd.query(s) for s in qs[:30]]
+    assert rc_again == st.STEINER_EINVAL and r_again is None
+    # continuous batching happened: queries joined while others were on the
+    # device, and far fewer kernel launches ran than there were queries
+    assert admitted == sum(1 for s in qs if len(s) > 1)
+    assert admitted_busy > 0
+    assert 0 < launches < len(qs)
     assert len(results) == len(tickets)
     res = [results[t] for t in tickets]
     _check(g, qs, res)

@@ -79,3 +79,24 @@ def test_noalloc_rejects_unsorted_seeds():
     rc = st.steiner_voronoi_noalloc(row_ptr, col, w, _dev(seeds), cell, None, None)
     assert rc == st.STEINER_OK
     np.testing.assert_array_equal(cell.cpu().numpy(), _reference(g, seeds)[0])
+
+
+def test_noalloc_rejects_bad_row_offsets_and_leaves_outputs_untouched():
+    """Row offsets that decrease, or that do not end at the arc count, are
+    caught before any arc is read; the outputs keep their contents; the
+    next call with good offsets works."""
+    g = wl.grid(40, 30, 9, seed=6)
+    col, w = _dev(g.col), _dev(g.w)
+    seeds = np.array([7, 50, 1100], np.int32)
+    bad = g.row_ptr.copy()
+    bad[100] = bad[102]                  # row 100 would start after its end
+    for rp, c in ((bad, col), (g.row_ptr, col[:-2])):    # decreasing; row_ptr[n] != n_arcs
+        cell = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+        rc = st.steiner_voronoi_noalloc(_dev(rp), c, w, _dev(seeds), cell, cell, cell)
+        assert rc == st.STEINER_EINVAL
+        assert "row_ptr" in st.last_error()
+        assert bool((cell == -7).all())
+    cell = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    rc = st.steiner_voronoi_noalloc(_dev(g.row_ptr), col, w, _dev(seeds), cell, None, None)
+    assert rc == st.STEINER_OK
+    np.testing.assert_array_equal(cell.cpu().numpy(), _reference(g, seeds)[0])
