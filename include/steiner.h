@@ -212,8 +212,19 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  converged (1..64, default 1: whole waves), or earlier
  *                  when a request waits and a slot is free
  *   "max_iters"    frontier iteration cap (STEINER_ETIMEOUT beyond it)
+ *   "far_scan"     how a band split finds the vertices left for later
+ *                  bands: -1 (default) chooses, 0 keeps a pile of them
+ *                  (one stamp exchange and queue slot per improvement),
+ *                  1 scans every label at the split instead
+ *   "label_bits"   width of the Voronoi labels: 0 (default) chooses per
+ *                  query, 32 or 64 force it.  A 32-bit label holds
+ *                  (distance << b) | rank with b the bits of the largest
+ *                  seed rank; a query whose distances do not fit runs again
+ *                  with 64-bit labels, so results never depend on the width
  * steiner_get_param also reads "sssp_max_blocks", "sm_count",
- * "heavy_chunks" and the multi-query engine's tracing counters
+ * "heavy_chunks", "label_bits_last" (the width the last query ended with),
+ * "narrow_reruns" (queries rerun with 64-bit labels) and the multi-query
+ * engine's tracing counters
  * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
  * microseconds, "batch_launches", "batch_iterations", "batch_items",
  * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds, "batch_admitted"

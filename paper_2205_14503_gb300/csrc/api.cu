@@ -49,6 +49,8 @@ cudaError_t dalloc(T *&p, uint64_t count) {
     return cudaMalloc((void **)&p, count * sizeof(T));
 }
 
+uint32_t bit_length(uint32_t x) { return x ? 32u - (uint32_t)__builtin_clz(x) : 0u; }
+
 uint32_t bits_for(uint32_t n) {
     uint32_t b = 1;
     while (b < 32 && (1ull << b) < (uint64_t)n) ++b;
@@ -69,6 +71,16 @@ struct steiner_graph {
     uint32_t delta = 0;
     uint32_t max_iters = 1u << 22;
     uint32_t local_rounds = 0;
+    // Label width of the Voronoi phase: 0 chooses per query (32 bits when
+    // the distance field leaves room for 256 largest weights and no query
+    // with as few distance bits has overflowed it before), 32 or 64 force it.
+    uint32_t label_bits = 0;
+    // Band splits: -1 chooses (a scan of the labels while the light/heavy
+    // split is on, else the far pile), 0 / 1 force the pile / the scan.
+    int far_scan = -1;
+    uint32_t narrow_fail_dbits = 0;   // most distance bits a narrow attempt ran out of
+    uint32_t last_label_bits = 0;
+    uint64_t narrow_reruns = 0;
     Control *h_ctl = nullptr;      // pinned
     cudaEvent_t ev[6] = {};
     BatchEngine *batch = nullptr;
@@ -83,6 +95,7 @@ int ensure_n_workspace(steiner_graph *G) {
     uint32_t n = G->g.n;
     ws.n = n;
     CK(dalloc(ws.label, n));
+    CK(dalloc(ws.label32, n));
     CK(dalloc(ws.pred_arc, n));
     CK(dalloc(ws.stamp_near, n));
     CK(dalloc(ws.stamp_far, n));
@@ -196,8 +209,9 @@ cudaError_t ensure_partition(steiner_graph *G, uint32_t delta) {
 }
 
 // Runs Steps 1 (and, with `full`, 2-7) of Algorithm 2 for one sorted seed
-// list.  Leaves the control block in G->h_ctl.
-int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, float *ms) {
+// list with the label width in G->ws.narrow.  Leaves the control block in
+// G->h_ctl.
+int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool full, float *ms) {
     uint32_t k = (uint32_t)ss.size();
     int rc = ensure_n_workspace(G);
     if (rc) return rc;
@@ -206,8 +220,14 @@ int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, fl
     Workspace &ws = G->ws;
     cudaStream_t s = G->stream;
     CK(cudaMemcpyAsync(ws.seeds, ss.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s));
+    // far scan: by default wherever the light/heavy split is on (a band's
+    // heavy-arc pass sends every proposal far, and the pile would cost a
+    // stamp exchange and a queue slot per improvement)
+    const bool split_on = G->delta <= G->g.max_w;
+    const uint32_t far_scan = G->far_scan < 0 ? (split_on ? 1u : 0u) : (uint32_t)G->far_scan;
+    static const bool trace = getenv("STEINER_TRACE") != nullptr;
     SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
-                 ws.epoch_band};
+                 ws.epoch_band, far_scan, trace ? 1u : 0u};
     CK(cudaEventRecord(G->ev[0], s));
     CK(ensure_partition(G, G->delta));
     CK(launch_init(G->g, ws, k, G->delta, s));
@@ -236,6 +256,34 @@ int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, fl
     }
     advance_epochs(ws, *G->h_ctl, s);
     return STEINER_OK;
+}
+
+// As run_pipeline_once, choosing the label width: 32-bit labels hold
+// (dist << rank bits) | rank; if a distance did not fit (ERR_NARROW) the
+// query runs again with 64-bit labels, so the result never depends on the
+// width.  ms[] (if given) sums both attempts.
+int run_pipeline(steiner_graph *G, const std::vector<int32_t> &ss, bool full, float *ms) {
+    const uint32_t k = (uint32_t)ss.size();
+    const uint32_t rbits = bits_for(k);
+    const uint32_t dbits = 32 - rbits;
+    bool narrow;
+    if (G->label_bits == 64) narrow = false;
+    else if (G->label_bits == 32) narrow = true;
+    else narrow = dbits >= bit_length(G->g.max_w) + 8 && dbits > G->narrow_fail_dbits;
+    G->ws.narrow = narrow;
+    G->ws.lshift = rbits;
+    int rc = run_pipeline_once(G, ss, full, ms);
+    G->last_label_bits = narrow ? 32 : 64;
+    if (rc || !narrow || !(G->h_ctl->err & ERR_NARROW)) return rc;
+    ++G->narrow_reruns;
+    G->narrow_fail_dbits = std::max(G->narrow_fail_dbits, dbits);
+    G->ws.narrow = false;
+    G->last_label_bits = 64;
+    float ms2[6] = {0, 0, 0, 0, 0, 0};
+    rc = run_pipeline_once(G, ss, full, ms ? ms2 : nullptr);
+    if (ms)
+        for (int i = 0; i < 6; ++i) ms[i] += ms2[i];
+    return rc;
 }
 
 int fetch_tree(steiner_graph *G, steiner_result_t *out) {
@@ -294,8 +342,9 @@ int query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_res
                     break;
                 }
             double us = t1 > c.trace_ns[i] ? 1e-3 * (double)(t1 - c.trace_ns[i]) : -1.0;
-            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u  %.1f us\n", i,
-                    c.trace[i][0], c.trace[i][1], c.trace[i][2], c.trace[i][3], us);
+            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u  %.1f us  relax %llu improved %llu\n",
+                    i, c.trace[i][0], c.trace[i][1], c.trace[i][2], c.trace[i][3], us,
+                    c.trace_relax[i][0], c.trace_relax[i][1]);
         }
     }
     if (rc == STEINER_OK || rc == STEINER_EDISCONNECTED) {
@@ -524,7 +573,7 @@ void steiner_free_graph(steiner_graph_t G) {
     cudaSetDevice(G->device);
     if (G->stream) cudaStreamSynchronize(G->stream);
     Workspace &ws = G->ws;
-    void *bufs[] = {ws.label, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.stamp_band, ws.band_q,
+    void *bufs[] = {ws.label, ws.label32, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.stamp_band, ws.band_q,
                     ws.band_hq, ws.mark, ws.q[0], ws.q[1],
                     ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
                     ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
@@ -556,6 +605,13 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     } else if (!strcmp(key, "local_rounds")) {
         if (value < 0 || value > 1024) return fail(STEINER_EINVAL, "local_rounds out of range");
         G->local_rounds = (uint32_t)value;
+    } else if (!strcmp(key, "far_scan")) {
+        if (value < -1 || value > 1) return fail(STEINER_EINVAL, "far_scan must be -1, 0 or 1");
+        G->far_scan = (int)value;
+    } else if (!strcmp(key, "label_bits")) {
+        if (value != 0 && value != 32 && value != 64)
+            return fail(STEINER_EINVAL, "label_bits must be 0 (automatic), 32 or 64");
+        G->label_bits = (uint32_t)value;
     } else if (!strcmp(key, "max_iters")) {
         if (value < 1 || value > 0x7FFFFFFF) return fail(STEINER_EINVAL, "max_iters out of range");
         G->max_iters = (uint32_t)value;
@@ -574,6 +630,10 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "sssp_max_blocks")) return G->geo.sssp_max_blocks;
     if (!strcmp(key, "sm_count")) return G->geo.sm_count;
     if (!strcmp(key, "heavy_chunks")) return G->g.n_heavy_chunks;
+    if (!strcmp(key, "label_bits")) return G->label_bits;
+    if (!strcmp(key, "far_scan")) return G->far_scan;
+    if (!strcmp(key, "label_bits_last")) return G->last_label_bits;
+    if (!strcmp(key, "narrow_reruns")) return (int64_t)G->narrow_reruns;
     if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);
     return -1;
 }

@@ -30,6 +30,8 @@ struct ScanArgs {
     uint32_t n_heavy_chunks;
     uint32_t n;
     const uint64_t *label;
+    const uint32_t *label32;         // narrow labels (the narrow kernel)
+    uint32_t lshift;
     uint32_t *pred_arc;
     uint64_t *pairtab;
     uint32_t k;
@@ -39,15 +41,23 @@ struct ScanArgs {
     const uint32_t *orig_row_ptr;
 };
 
+// Label of v in the 64-bit form.
+template <bool NARROW>
+__device__ __forceinline__ uint64_t scan_label(const ScanArgs &a, uint32_t v) {
+    if (NARROW) return widen_label(__ldg(&a.label32[v]), a.lshift);
+    return __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
+}
+
 // Arc `arc` of row v.  The bridge key carries the caller's arc index,
 // cbase + arc (cbase: the caller's row start of v minus v's internal row
 // start, taken once per row), so ties between equal bridges break on the
 // caller's CSR order whatever the internal vertex order.
+template <bool NARROW>
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
                                          uint32_t cbase, uint32_t arc, bool &overflow) {
     if (!valid) return;
     uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
-    uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[e.x]));
+    uint64_t lu = scan_label<NARROW>(a, e.x);
     if (lv == INF64 || lu == INF64) {
         // a reached vertex next to an unreached one: its true distance is
         // finite but did not fit below 2^32 - 1
@@ -71,6 +81,7 @@ __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t
     }
 }
 
+template <bool NARROW>
 __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -85,10 +96,10 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
             uint32_t rs = a.row_ptr[v];
             uint32_t s = rs + c * CHUNK;
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
-            uint64_t lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
+            uint64_t lv = scan_label<NARROW>(a, v);
             uint32_t cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, rs);
             for (uint32_t b = s; b < e; b += 32)
-                scan_arc(a, b + lane < e, v, lv, cbase, b + lane, overflow);
+                scan_arc<NARROW>(a, b + lane < e, v, lv, cbase, b + lane, overflow);
         } else {
             uint32_t v = (wi - a.n_heavy_chunks) * 32 + lane;
             uint32_t s = 0, deg = 0, cbase = 0;
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
                 s = a.row_ptr[v];
                 deg = a.row_ptr[v + 1] - s;
                 if (deg >= HEAVY_DEG) deg = 0;          // covered by the chunk list
-                lv = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
+                lv = scan_label<NARROW>(a, v);
                 if (deg) cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, s);
             }
             uint32_t incl = warp_inclusive_scan(deg);
@@ -112,7 +123,7 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
                 uint64_t lo = __shfl_sync(FULL, lv, owner);
                 uint32_t co = __shfl_sync(FULL, cbase, owner);
                 uint32_t vo = (wi - a.n_heavy_chunks) * 32 + owner;
-                scan_arc(a, valid, vo, lo, co, so + (j - eo), overflow);
+                scan_arc<NARROW>(a, valid, vo, lo, co, so + (j - eo), overflow);
             }
         }
     }
@@ -242,6 +253,8 @@ cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs
     a.n_heavy_chunks = g.n_heavy_chunks;
     a.n = g.n;
     a.label = ws.label;
+    a.label32 = ws.label32;
+    a.lshift = ws.lshift;
     a.pred_arc = ws.pred_arc;
     a.pairtab = ws.pairtab;
     a.k = k;
@@ -259,7 +272,8 @@ cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs
     const uint64_t cap = (uint64_t)current_sm_count() * 32;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+    if (ws.narrow) scan_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else scan_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,19 @@ enum : uint32_t {
     ERR_TIMEOUT = 2u,       // iteration cap hit
     ERR_CAPACITY = 4u,      // an append would have overrun its buffer (skipped)
     ERR_BARRIER = 8u,       // a grid barrier wait gave up
+    ERR_NARROW = 16u,       // a distance did not fit a 32-bit label (rerun with 64 bits)
 };
+
+// Labels.  The 64-bit form is (dist << 32) | rank.  The narrow 32-bit form
+// is (dist << shift) | rank with shift = the bits of the largest rank, for
+// distances up to (2^(32 - shift)) - 2; both order lexicographically by
+// (dist, rank), so an atomicMin on either finds the same fixed point.  The
+// all-ones word is "unreached" in both.  widen_label maps the narrow form
+// to the 64-bit one.
+__host__ __device__ __forceinline__ uint64_t widen_label(uint32_t l, uint32_t shift) {
+    if (l == 0xFFFFFFFFu) return ~0ull;
+    return ((uint64_t)(l >> shift) << 32) | (l & ((1u << shift) - 1u));
+}
 
 // Spin limit of a grid barrier wait (each spin sleeps ~64 ns): ~4 s.
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;

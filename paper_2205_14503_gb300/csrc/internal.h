@@ -94,6 +94,7 @@ struct Control {
     uint32_t bands;
     uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
     unsigned long long trace_ns[TRACE_LEN];   // their start times (global timer, ns)
+    unsigned long long trace_relax[TRACE_LEN][2];   // relaxations, improvements (when traced)
     unsigned long long end_ns;                // end of the last iteration
 };
 
@@ -101,6 +102,11 @@ struct Control {
 struct Workspace {
     uint32_t n = 0;
     uint64_t *label = nullptr;      // (dist << 32) | rank
+    // Narrow labels (dist << lshift) | rank, used instead of `label` by the
+    // Voronoi, scan and export kernels of a query with `narrow` set.
+    uint32_t *label32 = nullptr;
+    uint32_t lshift = 0;
+    bool narrow = false;
     uint32_t *pred_arc = nullptr;   // arc of the pred edge in v's row; SEED_ARC; INF32
     uint32_t pred_stride = 1;       // pred of v at pred_arc[v * pred_stride]
     uint32_t *stamp_near = nullptr;
@@ -152,6 +158,8 @@ struct SsspParams {
     uint32_t base_far;       // first far tag of this query
     uint32_t local_rounds;   // warp-local relaxation rounds per iteration
     uint32_t base_band;      // first band-list tag of this query
+    uint32_t far_scan;       // splits scan the labels instead of a far pile
+    uint32_t trace;          // per-iteration relaxation counts into Control::trace_relax
 };
 
 // SM count of the current device (queried once per device, then cached);

@@ -33,7 +33,10 @@ struct SsspArgs {
     const uint32_t *__restrict__ row_ptr;
     const uint2 *__restrict__ adj;
     uint32_t n;
-    uint64_t *label;
+    uint64_t *label;         // 64-bit labels (the wide kernel)
+    uint32_t *label32;       // narrow labels (the narrow kernel)
+    uint32_t lshift;         // rank bits of a narrow label
+    uint32_t ldmax;          // largest distance a narrow label holds
     uint32_t *stamp_near;
     uint32_t *stamp_far;
     uint32_t *q0, *q1;
@@ -51,6 +54,8 @@ struct SsspArgs {
     uint64_t *band_hq;       // heavy-row chunks of listed high-degree vertices
     uint32_t base_band;
     uint32_t defer;          // light/heavy arc split on
+    uint32_t far_scan;       // no far pile: splits find far vertices by scanning the labels
+    uint32_t trace;          // record per-iteration relaxation counts
     // with the split: end of each row's light part in the weight-partitioned
     // adjacency `adj` (null: rows are unpartitioned and arcs are filtered)
     const uint32_t *lend;
@@ -62,9 +67,11 @@ struct SsspArgs {
 // ---------------------------------------------------------------------------
 
 __global__ void init_labels_kernel(uint32_t n, uint64_t *__restrict__ label,
+                                   uint32_t *__restrict__ label32,
                                    uint32_t *__restrict__ pred_arc) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        label[v] = INF64;
+        if (label32) label32[v] = INF32;
+        else label[v] = INF64;
         pred_arc[v] = INF32;
     }
 }
@@ -72,7 +79,8 @@ __global__ void init_labels_kernel(uint32_t n, uint64_t *__restrict__ label,
 __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr,
                                   const uint32_t *__restrict__ lend, const int32_t *seeds,
                                   const uint32_t *__restrict__ new_of,
-                                  uint32_t k, uint64_t *label, uint32_t *pred_arc,
+                                  uint32_t k, uint64_t *label, uint32_t *label32,
+                                  uint32_t *pred_arc,
                                   uint32_t *stamp_near, uint32_t tag0, uint32_t *q0,
                                   uint64_t *hq0, uint32_t heavy_cap, uint32_t n, Control *ctl) {
     uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +90,8 @@ __global__ void init_seeds_kernel(const uint32_t *__restrict__ row_ptr,
     }
     if (r >= k) return;
     uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
-    label[s] = (uint64_t)r;               // distance 0, cell = rank r
+    if (label32) label32[s] = r;          // distance 0, cell = rank r
+    else label[s] = (uint64_t)r;
     pred_arc[s] = SEED_ARC;
     stamp_near[s] = tag0;
     uint32_t rs = row_ptr[s], deg = (lend ? lend[s] : row_ptr[s + 1]) - rs;   // near part
@@ -219,6 +228,13 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
     }
 }
 
+// Label of v in the 64-bit form (read past L1: other blocks write it).
+template <bool NARROW>
+__device__ __forceinline__ uint64_t sssp_label(const SsspArgs &a, uint32_t v) {
+    if (NARROW) return widen_label(ldcg_u32(&a.label32[v]), a.lshift);
+    return ldcg_u64(&a.label[v]);
+}
+
 // Relaxes up to ILP arcs per lane.  For arc u of this lane: valid[u], the
 // arc index and the tail's label; only arcs with wlo <= weight < whi are
 // relaxed.  The loads and atomics of the ILP arcs are issued back to back
@@ -227,12 +243,16 @@ __device__ __forceinline__ void push_far(const SsspArgs &a, Stage &st, const Pus
 // improving proposals issue the atomic: right for thick frontiers, where
 // L2 atomic throughput is the limit; thin frontiers are latency-bound and
 // skip the extra dependent load.
+// The tail labels lab[] are in the 64-bit form; NARROW kernels keep the
+// head labels in 32 bits and flag (narrow_miss) any proposal whose distance
+// does not fit one, which the host answers with a 64-bit rerun.
+template <bool NARROW>
 __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const PushTargets &t,
                                             const bool (&valid)[ILP], const uint32_t (&arc)[ILP],
                                             const uint64_t (&lab)[ILP], bool precheck,
                                             bool stream, uint32_t wlo, uint32_t whi,
                                             unsigned long long &attempts,
-                                            unsigned long long &improved) {
+                                            unsigned long long &improved, bool &narrow_miss) {
     uint2 e[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
@@ -250,8 +270,18 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         if (valid[u] && e[u].y >= wlo && e[u].y < whi) {
             ++attempts;
             nd[u] = (lab[u] >> 32) + (uint64_t)e[u].y;
-            // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
-            if (nd[u] < INF32) {
+            if (NARROW) {
+                if (nd[u] > a.ldmax) {
+                    narrow_miss = true;
+                } else {
+                    const uint32_t nl = ((uint32_t)nd[u] << a.lshift) | (uint32_t)lab[u];
+                    if (!precheck || nl < ldcg_u32(&a.label32[e[u].x])) {
+                        const uint32_t old = atomicMin(&a.label32[e[u].x], nl);
+                        imp[u] = nl < old;
+                    }
+                }
+            } else if (nd[u] < INF32) {
+                // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
                 uint64_t nl = (nd[u] << 32) | (lab[u] & 0xFFFFFFFFull);
                 if (!precheck || nl < ldcg_u64(&a.label[e[u].x])) {
                     uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
@@ -282,8 +312,9 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                                          : atomicExch(&a.stamp_near[v], t.tag_next)) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
-            cand[u] = true;
-            to_far[u] = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
+            cand[u] = true;      // bounds far_min
+            // with the far scan, the split finds far vertices by their labels
+            if (!a.far_scan) to_far[u] = atomicExch(&a.stamp_far[v], t.tag_far) != t.tag_far;
         }
     }
 #pragma unroll
@@ -337,6 +368,7 @@ __device__ __forceinline__ void band_track_heavy(const SsspArgs &a, uint32_t u, 
 // the persistent near/far kernel
 // ---------------------------------------------------------------------------
 
+template <bool NARROW>
 __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     __shared__ Stage st;
     const uint32_t lane = lane_id();
@@ -344,6 +376,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     Control *ctl = a.ctl;
     unsigned long long attempts = 0, improved = 0;
+    bool narrow_miss = false;
+    unsigned long long att0 = 0, imp0 = 0;     // counts at the start of the iteration (trace)
     uint32_t it = 0, phase = 0, bands = 0;
     uint64_t T = a.delta;
     bool first = (blockIdx.x == 0 && threadIdx.x == 0);
@@ -409,7 +443,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 const uint32_t base = hp && a.lend ? le : r0, end = hp ? r1 : le;
                 uint32_t s = base + c * CHUNK;
                 uint32_t e = min(end, s + CHUNK);
-                uint64_t lab = ldcg_u64(&a.label[u]);
+                uint64_t lab = sssp_label<NARROW>(a, u);
                 if (track && c == 0) band_track_heavy(a, u, a.lend ? r1 - le : r1 - r0, tag_band);
                 for (uint32_t b = s; b < e; b += 32 * ILP) {
                     bool valid[ILP];
@@ -421,8 +455,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         valid[q] = arc[q] < e;
                         labs[q] = lab;
                     }
-                    relax_group(a, st, t, valid, arc, labs, true, true, wlo, whi, attempts,
-                                improved);
+                    relax_group<NARROW>(a, st, t, valid, arc, labs, true, true, wlo, whi, attempts,
+                                improved, narrow_miss);
                 }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
@@ -442,7 +476,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         deg = le - r0;
                         hdeg = a.lend ? r1 - le : r1 - r0;
                     }
-                    lab = ldcg_u64(&a.label[u]);
+                    lab = sssp_label<NARROW>(a, u);
                     if (lab == INF64) deg = 0;
                 }
                 if (track) band_track(a, has, u, hdeg, tag_band);
@@ -463,8 +497,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         labs[q] = __shfl_sync(FULL, lab, owner);
                         arc[q] = so + (j - eo);
                     }
-                    relax_group(a, st, t, valid, arc, labs, bsz == 32, false, wlo, whi,
-                                attempts, improved);
+                    relax_group<NARROW>(a, st, t, valid, arc, labs, bsz == 32, false, wlo, whi,
+                                attempts, improved, narrow_miss);
                 }
             }
         }
@@ -499,7 +533,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         exch_acquire(&a.stamp_near[u], tag_cur);   // later improvements re-push u
                         deg = le - s;
                         hdeg = a.lend ? r1 - le : r1 - s;
-                        lab = ldcg_u64(&a.label[u]);
+                        lab = sssp_label<NARROW>(a, u);
                     }
                     if (track) band_track(a, has, u, hdeg, tag_band);
                     uint32_t incl = warp_inclusive_scan(deg);
@@ -519,13 +553,27 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                             labs[q] = __shfl_sync(FULL, lab, owner);
                             arc[q] = so + (j - eo);
                         }
-                        relax_group(a, st, t, valid, arc, labs, false, false, wlo, whi,
-                                    attempts, improved);
+                        relax_group<NARROW>(a, st, t, valid, arc, labs, false, false, wlo, whi,
+                                    attempts, improved, narrow_miss);
                     }
                 }
                 lo = hi;
             }
             if (lane == 0) st.local_lo[wib] = lo;
+        }
+        if (a.trace && it < TRACE_LEN) {
+            unsigned long long da = attempts - att0, di = improved - imp0;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                da += __shfl_xor_sync(FULL, da, o);
+                di += __shfl_xor_sync(FULL, di, o);
+            }
+            if (lane == 0 && (da | di)) {
+                atomicAdd(&ctl->trace_relax[it][0], da);
+                atomicAdd(&ctl->trace_relax[it][1], di);
+            }
+            att0 = attempts;
+            imp0 = improved;
         }
         flush_stage(st, t, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
@@ -564,12 +612,15 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         // the barrier that ends the split.  Iteration it + 1 will push into
         // slot (it + 2) % 3, which the skipped top of iteration it would
         // have cleared: clear it here (its last reader was iteration it - 1).
+        // With the far scan there is no pile: every label at or above the
+        // threshold came from a proposal (or a split) that lowered far_min,
+        // so an infinite far_min means no vertex is left unsettled.
         uint32_t nf = min(ldcg_u32(&ctl->far_count[fc]), a.n);
-        if (nf == 0) {                                        // converged
+        uint32_t fmin = ldcg_u32(&ctl->far_min[fc]);
+        if (a.far_scan ? fmin == INF32 : nf == 0) {           // converged
             if (first) ctl->exit_reason = 1;
             break;
         }
-        uint32_t fmin = ldcg_u32(&ctl->far_min[fc]);
         uint64_t T_old = T;
         T = (fmin != INF32 && (uint64_t)fmin > T ? (uint64_t)fmin : T) + a.delta;
         ++phase;
@@ -593,15 +644,18 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.tag_next = a.base_near + its;
         u.tag_far = a.base_far + phase;
         u.T = T;
-        for (uint32_t b = warp * 32; b < nf; b += nwarps * 32) {
+        // the far pile, or with the far scan every vertex (coalesced labels)
+        const uint32_t n_split = a.far_scan ? a.n : nf;
+        for (uint32_t b = warp * 32; b < n_split; b += nwarps * 32) {
             uint32_t i = b + lane;
-            bool valid = i < nf;
+            bool valid = i < n_split;
             uint32_t v = 0, deg = 0;
             uint64_t d = INF32;
             if (valid) {
-                v = ldcg_u32(&fs[i]);
-                d = ldcg_u64(&a.label[v]) >> 32;
+                v = a.far_scan ? i : ldcg_u32(&fs[i]);
+                d = sssp_label<NARROW>(a, v) >> 32;
             }
+            valid = valid && d != INF32;                      // unreached
             bool to_near = valid && d >= T_old && d < T;     // below T_old: already settled
             bool keep = valid && d >= T;
             if (to_near) {
@@ -610,7 +664,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 deg = r1 - r0;
             }
             const bool cand = keep;
-            if (keep) keep = atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
+            if (keep) keep = !a.far_scan && atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
             push_near(a, st, u, to_near, v, deg);
             push_far(a, st, u, keep, cand, v, (uint32_t)d);
         }
@@ -642,6 +696,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         atomicAdd(&ctl->relax_attempts, attempts);
         atomicAdd(&ctl->relax_improved, improved);
     }
+    if (NARROW && __any_sync(FULL, narrow_miss) && lane == 0) atomicOr(&ctl->err, ERR_NARROW);
     if (first) {
         ctl->iterations = it;
         ctl->phases = phase;
@@ -655,13 +710,14 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
 
 __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
                               const uint64_t *__restrict__ label,
+                              const uint32_t *__restrict__ label32, uint32_t lshift,
                               const uint32_t *__restrict__ pred_arc,
                               const int32_t *__restrict__ seeds,
                               const uint32_t *__restrict__ orig_of, int32_t *cell, uint32_t *dist,
                               int32_t *pred) {
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         const uint32_t v = caller_id(orig_of, u);       // outputs are in the caller's ids
-        uint64_t lab = label[u];
+        uint64_t lab = label32 ? widen_label(label32[u], lshift) : label[u];
         if (lab == INF64) {
             if (cell) cell[v] = -1;
             if (dist) dist[v] = INF32;
@@ -694,20 +750,25 @@ cudaError_t launch_init(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t d
                         cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ws.ctl, 0, sizeof(Control), s);
     if (e != cudaSuccess) return e;
-    init_labels_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, ws.label, ws.pred_arc);
+    uint32_t *l32 = ws.narrow ? ws.label32 : nullptr;
+    init_labels_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, ws.label, l32, ws.pred_arc);
     init_seeds_kernel<<<(k + 255) / 256, 256, 0, s>>>(g.row_ptr, active_lend(g, delta), ws.seeds,
-                                                       g.new_of, k, ws.label,
+                                                       g.new_of, k, ws.label, l32,
                                                        ws.pred_arc, ws.stamp_near,
                                                        ws.epoch_near, ws.q[0], ws.hq[0],
                                                        g.heavy_chunk_cap, g.n, ws.ctl);
     return cudaGetLastError();
 }
 
+// Co-resident blocks per SM that both label widths of the kernel reach.
 int sssp_occupancy(int threads) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, threads, 0) != cudaSuccess)
+    int nw = 0, nn = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, sssp_kernel<false>, threads, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nn, sssp_kernel<true>, threads, 0) !=
+            cudaSuccess)
         return 0;
-    return nb;
+    return nw < nn ? nw : nn;
 }
 
 cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
@@ -717,6 +778,9 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.adj = g.adj;
     a.n = g.n;
     a.label = ws.label;
+    a.label32 = ws.label32;
+    a.lshift = ws.lshift;
+    a.ldmax = (uint32_t)((1ull << (32 - ws.lshift)) - 2);
     a.stamp_near = ws.stamp_near;
     a.stamp_far = ws.stamp_far;
     a.q0 = ws.q[0];
@@ -737,18 +801,22 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.band_hq = ws.band_hq;
     a.base_band = p.base_band;
     a.defer = p.delta <= g.max_w ? 1u : 0u;
+    a.far_scan = p.far_scan;
+    a.trace = p.trace;
     a.lend = active_lend(g, p.delta);
     if (a.lend) a.adj = g.adj_w;        // rows partitioned by weight class
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)sssp_kernel, dim3(geo.sssp_blocks),
-                                       dim3(geo.threads), args, 0, s);
+    const void *fn = ws.narrow ? (const void *)sssp_kernel<true> : (const void *)sssp_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(geo.sssp_blocks), dim3(geo.threads), args, 0, s);
 }
 
 cudaError_t launch_export(const DevGraph &g, Workspace &ws, uint32_t k, int32_t *cell,
                           uint32_t *dist, int32_t *pred, cudaStream_t s) {
     (void)k;
-    export_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.adj, ws.label, ws.pred_arc,
-                                                      ws.seeds, g.orig_of, cell, dist, pred);
+    export_kernel<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.adj, ws.label,
+                                                      ws.narrow ? ws.label32 : nullptr, ws.lshift,
+                                                      ws.pred_arc, ws.seeds, g.orig_of, cell,
+                                                      dist, pred);
     return cudaGetLastError();
 }
 

@@ -308,3 +308,75 @@ def test_block_local_rounds_on_grids(local):
         np.testing.assert_array_equal(dist, ref.dist)
         np.testing.assert_array_equal(pred, ref.pred)
         np.testing.assert_array_equal(res.edges, ref.edges)
+
+
+def _compare_forced(g, seeds, **params):
+    """_compare with handle parameters set first; returns the handle's
+    label-width counters after the two calls."""
+    ref = oracle.steiner(g, seeds, want_labels=True, want_pairs=True)
+    with st.SteinerGraph(g) as Gd:
+        for key, value in params.items():
+            Gd.set_param(key, value)
+        rc, cell, dist, pred = Gd.voronoi(seeds)
+        res = Gd.query_detail(seeds)
+        counters = {k: Gd.get_param(k) for k in ("label_bits_last", "narrow_reruns")}
+    assert rc == st.STEINER_OK and res.status == ref.status == oracle.OK, st.last_error()
+    np.testing.assert_array_equal(cell, ref.cell)
+    np.testing.assert_array_equal(dist, ref.dist)
+    np.testing.assert_array_equal(pred, ref.pred)
+    np.testing.assert_array_equal(res.pairs[:, :4], ref.pairs)
+    np.testing.assert_array_equal(res.edges, ref.edges)
+    assert res.total == ref.total
+    return counters
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_label_width_forced(bits):
+    """Both label widths reach the oracle's fixed point: a 32-bit label
+    packs (distance << rank bits) | rank, a 64-bit one (distance << 32) |
+    rank, both ordered by (distance, rank).  Hubs in chunked rows with many
+    seeds, unit weights (maximal ties), a grid with the light/heavy split,
+    and a sparse random graph."""
+    cases = [(wl.rmat(14, 16, wmax=1000, seed=41), 500, True),
+             (wl.rmat(12, 16, wmax=1, seed=42), 200, True),
+             (wl.grid(150, 110, 1000, seed=43), 60, False),
+             (G.random_connected(3000, 2000, 1, 50, 44), 30, False)]
+    for g, k, lcc in cases:
+        pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
+        seeds = wl.sample_distinct(pool, k, 40 + k)
+        for delta in (None, 150):
+            params = {"label_bits": bits} if delta is None else {"label_bits": bits, "delta": delta}
+            c = _compare_forced(g, seeds, **params)
+            assert c == {"label_bits_last": bits, "narrow_reruns": 0}
+
+
+def test_narrow_labels_fall_back_to_64_bits():
+    """A query whose distances do not fit a 32-bit label is rerun with
+    64-bit labels and still equals the oracle.  Here 4096 seeds sit at one
+    end of a 50,000-vertex path (12 rank bits leave 20 distance bits, so
+    distances up to about 10^6) and the far end lies about 2 * 10^7 away.
+    The automatic choice picks 32 bits (weights below 512 leave 11 spare
+    bits), falls back once, and then takes 64 bits up front for queries
+    with as few distance bits."""
+    n = 50_000
+    rng = np.random.default_rng(7)
+    g = wl.from_edges(n, np.arange(n - 1), np.arange(1, n), rng.integers(400, 512, n - 1))
+    seeds = np.arange(4096, dtype=np.int32)
+    c = _compare_forced(g, seeds, label_bits=32)
+    assert c == {"label_bits_last": 64, "narrow_reruns": 2}
+    c = _compare_forced(g, seeds)
+    assert c == {"label_bits_last": 64, "narrow_reruns": 1}
+
+
+@pytest.mark.parametrize("far_scan", [0, 1])
+@pytest.mark.parametrize("delta,local", [(50, 0), (999, 8), (5000, 0), (5000, 16)])
+def test_band_split_by_pile_or_scan(far_scan, delta, local):
+    """A band split finds the vertices left for later bands either from a
+    pile of far proposals or by scanning every label; both, with and without
+    the light/heavy split and warp-local rounds, give the oracle's labels,
+    distance graph and tree."""
+    for g, k, lcc in ((wl.grid(150, 110, 1000, seed=51), 60, False),
+                      (wl.rmat(12, 48, wmax=1000, seed=52), 25, True)):
+        pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
+        seeds = wl.sample_distinct(pool, k, 50 + k)
+        _compare_forced(g, seeds, far_scan=far_scan, delta=delta, local_rounds=local)
