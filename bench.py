@@ -3,9 +3,12 @@
 
 One step = one query through the whole path (Voronoi cells, predecessor and
 bridge scan, pair compaction, MST, expansion, sorted tree and total) on the
-plain high-diameter workload: a 4096 x 4096 4-connected grid with weights
-uniform in [1, 1000] and 256 seeds drawn uniformly over the grid.  Inputs
-(graph and seed set) are seeded and synthetic.
+largest single-query workload: an R-MAT scale-26 graph (67M vertices, 2.1G
+arcs, weights uniform in [1, 1000]) with 10,000 seeds drawn uniformly from
+its largest component (``--workload 2`` runs the 4096 x 4096 grid with 256
+seeds, ``--workload 1`` R-MAT 16 with 16 seeds).  Inputs (graph and seed
+set) are seeded and synthetic.  The autotuner tunes on another seed set of
+the same size from the same pool, never on the timed one.
 
 Printed (rank 0, one JSON line):
   value      trees/s from device time (CUDA events on the library's stream,
@@ -15,7 +18,9 @@ Printed (rank 0, one JSON line):
              edges out (copies inside the timed region)
   roofline   the Voronoi SSSP kernel's algorithmic bytes per launch / its
              event-timed duration, against the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle timed on the host cores (rank 0, N = 1)
+  cpu_baseline  the CPU oracle timed on one host core on one whole query
+             of the workload (rank 0, N = 1), run in a child process forked
+             before any CUDA call so it overlaps the GPU measurement
 
 ``--impl reference`` times the CPU oracle itself on the same workload.
 Multi-GPU: ``torchrun --nproc-per-node N bench.py --gpus N``; ranks are
@@ -39,7 +44,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = 2            # the 4096^2 grid, 256 seeds
+WORKLOAD = 3            # R-MAT scale 26, 10,000 seeds
+GRID = 2                # the 4096^2 grid, 256 seeds
+TUNE_SALT = 0x7E57      # seed-set salt of the autotuner's held-out sample
+REF_BUDGET_S = 300.0    # reference arm: whole oracle queries within this time
 SSSP_SOURCES = ["paper_2205_14503_gb300/csrc/voronoi.cu", "paper_2205_14503_gb300/csrc/common.cuh",
                 "paper_2205_14503_gb300/csrc/internal.h"]
 
@@ -160,40 +168,83 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 def workload(rank: int, side: int | None = None, k: int | None = None, cfg: int = WORKLOAD):
-    """The benchmark graph and seed set.  ``side``/``k`` shrink the grid for
-    profiling captures (same seed density); ``cfg`` picks another
-    single-query workload (1 R-MAT 16, 3 R-MAT 26); the default is the grid."""
+    """The benchmark graph, the timed seed set and the autotuner's held-out
+    seed set (same size, same pool, another salt).  ``side``/``k`` shrink
+    the grid for profiling captures (same seed density); ``cfg`` picks the
+    single-query workload (3 R-MAT 26, the default; 2 the grid; 1 R-MAT 16)."""
     import paper_2205_14503_gb300.workloads as wl
     if side:
-        g = wl.grid(side, side, 1000, wl.CONFIG_SEED + WORKLOAD)
-        seeds = wl.sample_distinct(np.arange(g.n, dtype=np.int32), k or 64,
-                                   (wl.CONFIG_SEED + WORKLOAD) ^ 0x51ED)
+        g = wl.grid(side, side, 1000, wl.CONFIG_SEED + GRID)
+        pool = np.arange(g.n, dtype=np.int32)
+        seeds = wl.sample_distinct(pool, k or 64, (wl.CONFIG_SEED + GRID) ^ 0x51ED)
     else:
         g = wl.config_graph(cfg)
         seeds = wl.config_seed_sets(cfg, g)[0]
+        pool = np.arange(g.n, dtype=np.int32) if cfg == GRID else wl.largest_cc(g)
     if rank > 0:    # replicas run their own queries of the same size
-        pool = np.arange(g.n, dtype=np.int32) if side or cfg == WORKLOAD else wl.largest_cc(g)
         seeds = wl.sample_distinct(pool, seeds.size, 0x5EED + cfg + 1000 * rank)
-    return g, seeds
+    tune_seeds = wl.sample_distinct(pool, seeds.size, 0x5EED + cfg + TUNE_SALT + 1000 * rank)
+    return g, seeds, tune_seeds
 
 
-def cpu_oracle_time(g, seeds, budget_s: float = 30.0):
-    """Time the oracle on whole queries until ~budget_s of CPU work."""
-    import oracle
-    times = []
-    t_all = time.perf_counter()
+def host_info() -> dict:
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemTotal:"):
+                    ram = round(int(line.split()[1]) / 2 ** 20, 1)
+    except OSError:
+        pass
+    import platform
+    return {"host_cores": os.cpu_count(), "host_ram_gib": ram, "machine": platform.machine()}
+
+
+def start_oracle_child(g, seeds):
+    """Forks a child that times one whole oracle query of (g, seeds) on one
+    host core and writes the result to a pipe.  Call before any CUDA call in
+    this process (a fork after CUDA initialisation is not safe)."""
+    r, w = os.pipe()
+    pid = os.fork()
+    if pid == 0:        # child: no CUDA here
+        os.close(r)
+        try:
+            import oracle
+            t0 = time.perf_counter()
+            res = oracle.steiner(g, seeds, want_labels=False)
+            dt = time.perf_counter() - t0
+            msg = {"seconds": dt, "status": int(res.status), "total": int(res.total),
+                   "edges_sha": hashlib.sha256(np.ascontiguousarray(res.edges, np.uint32)
+                                               .tobytes()).hexdigest()}
+        except Exception as e:      # reported, not raised, in the parent
+            msg = {"error": repr(e)}
+        data = json.dumps(msg).encode()
+        while data:
+            data = data[os.write(w, data):]
+        os._exit(0)
+    os.close(w)
+    return pid, r
+
+
+def finish_oracle_child(child):
+    pid, r = child
+    chunks = []
     while True:
-        t0 = time.perf_counter()
-        r = oracle.steiner(g, seeds, want_labels=False)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all + times[-1] > budget_s or len(times) >= 3:
+        b = os.read(r, 65536)
+        if not b:
             break
-    return r, times
+        chunks.append(b)
+    os.close(r)
+    os.waitpid(pid, 0)
+    try:
+        return json.loads(b"".join(chunks).decode())
+    except ValueError:
+        return {"error": "oracle child gave no result"}
 
 
 def config_dict(g, seeds, cfg: int = WORKLOAD, side: int | None = None):
     import paper_2205_14503_gb300.workloads as wl
-    if side or cfg == WORKLOAD:
+    if side or cfg == GRID:
         s = int(round(g.n ** 0.5))
         name, desc = f"grid{s}_k{seeds.size}", f"{s}x{s} 4-connected grid, w~U[1,1000]"
     else:
@@ -204,35 +255,59 @@ def config_dict(g, seeds, cfg: int = WORKLOAD, side: int | None = None):
     return {"workload": name, "graph": desc,
             "n": int(g.n), "arcs": int(g.n_arcs), "k": int(seeds.size),
             "l2": f"inputs larger than L2 (adjacency {g.n_arcs * 8 >> 20} MiB, "
-                  f"labels {g.n * 8 >> 20} MiB)"}
+                  f"labels {g.n * 4 >> 20}-{g.n * 8 >> 20} MiB)",
+            "tuning_seeds": f"held-out set of the same size (salt {TUNE_SALT:#x})"}
 
 
 METRIC = "Steiner trees/s (Voronoi SSSP + bridge scan + MST + expansion)"
 
 
 def run_reference(args, world, rank):
+    """The oracle itself (the paper ships no code) on the same workload,
+    metric and unit: each step is one whole query on one host core.  A
+    whole query of the R-MAT 26 workload takes minutes, so the arm times
+    whole queries within REF_BUDGET_S (at least one) and states in its line
+    how many it ran against the steps asked for; the oracle has nothing to
+    warm up, so no warm-up query runs when the budget is that short."""
     if rank != 0:
         return
-    g, seeds = workload(0, args.side, args.k, args.workload)
+    g, seeds, _ = workload(0, args.side, args.k, args.workload)
     import oracle
-    for _ in range(args.warmup):
-        oracle.steiner(g, seeds, want_labels=False)
     times = []
+    t_all = time.perf_counter()
+    warm = 0
+    while warm < args.warmup:
+        t0 = time.perf_counter()
+        oracle.steiner(g, seeds, want_labels=False)
+        warm += 1
+        if (args.steps + args.warmup) * (time.perf_counter() - t0) > REF_BUDGET_S:
+            break
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.steiner(g, seeds, want_labels=False)
         times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all + times[-1] > REF_BUDGET_S:
+            break
     total = sum(times)
-    value = args.steps / total
+    value = len(times) / total
+    per_q = total / len(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": len(times), "warmup": warm,
+            "ms_per_step": 1e3 * per_q, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": config_dict(g, seeds, args.workload, args.side),
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "trees/s", "cores": 1,
-                             "sample": "whole queries of the workload, single-threaded C oracle"},
+                             "sample": f"{len(times)} whole queries of the workload, "
+                                       "single-threaded C oracle", **host_info()},
             "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if len(times) < args.steps or warm < args.warmup:
+        line["requested"] = {"steps": args.steps, "warmup": args.warmup}
+        line["note"] = (f"one whole oracle query of this workload takes {per_q:.0f} s here; "
+                        f"{args.steps + args.warmup} of them would take "
+                        f"{(args.steps + args.warmup) * per_q / 60:.0f} min, so the arm timed "
+                        f"{len(times)} whole queries (and {warm} warm-up) within "
+                        f"{REF_BUDGET_S:.0f} s")
     print(json.dumps(line), flush=True)
 
 
@@ -242,25 +317,34 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     from paper_2205_14503_gb300 import steiner as st
 
+    g, seeds, tune_seeds = workload(rank, args.side, args.k, args.workload)
+    # the CPU baseline runs beside the GPU measurement, in a child forked
+    # before this process makes its first CUDA call
+    child = (start_oracle_child(g, seeds)
+             if world == 1 and rank == 0 and not args.no_cpu_baseline else None)
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)
-    g, seeds = workload(rank, args.side, args.k, args.workload)
     t0 = time.perf_counter()
     G = st.SteinerGraph(g, device=local)
     load_s = time.perf_counter() - t0
     tuned = None
     if args.tuned:
         # explicit (delta, blocks, local rounds), e.g. for profiling captures
-        d, b, lr = (int(x) for x in args.tuned.split(","))
+        vals = [int(x) for x in args.tuned.split(",")]
+        d, b, lr, lb, fs = vals + [0, 0, 0, 0, -1][len(vals):]
         G.set_param("delta", d)
         G.set_param("sssp_blocks", b)
         G.set_param("local_rounds", lr)
-        tuned = {"delta": d, "sssp_blocks": G.get_param("sssp_blocks"), "local_rounds": lr}
+        G.set_param("label_bits", lb)
+        G.set_param("far_scan", fs)
+        tuned = {"delta": d, "sssp_blocks": G.get_param("sssp_blocks"), "local_rounds": lr,
+                 "label_bits": lb, "far_scan": fs}
     elif not args.no_autotune:
-        # set-up, untimed: band width and persistent grid size for this graph
+        # set-up, untimed: band width, grid size, label width and split mode
+        # for this graph, tuned on the held-out seed set
         from paper_2205_14503_gb300 import autotune
-        tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
+        tuned = autotune.tune(G, g, [tune_seeds], cache_path=None, device=local)
     for _ in range(max(args.warmup, 3)):
         r = G.query_detail(seeds, pairs=False)
         if r.status != st.STEINER_OK:
@@ -305,7 +389,12 @@ def run_ours(args, world, rank, local):
     value = total_q / dev_s
     n, m_arcs = g.n, g.n_arcs
     sssp_ms = statistics.mean(phase["ms_voronoi"])
-    alg_bytes = 16 * m_arcs + 12 * n          # per SSSP launch (one query)
+    # per SSSP launch (one query): every arc record (8 B) and the head's
+    # label once, every row offset and label once; labels are 4 or 8 bytes
+    label_bits = G.get_param("label_bits_last")
+    lb = label_bits // 8
+    alg_bytes = (8 + lb) * m_arcs + (4 + lb) * n
+    narrow_reruns = G.get_param("narrow_reruns")
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (sssp_ms / 1e3) / 1e9
     cfgd = config_dict(g, seeds, args.workload, args.side)
@@ -320,6 +409,8 @@ def run_ours(args, world, rank, local):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                     "alg_bytes_rule": f"(8 + {lb}) B per arc + (4 + {lb}) B per vertex "
+                                       f"({label_bits}-bit labels)",
                      "launch_ms": sssp_ms},
         "e2e": {"value": total_q / e2e_s, "unit": "trees/s",
                 "h2d_bytes_per_step": int(seeds.size * 4),
@@ -335,19 +426,28 @@ def run_ours(args, world, rank, local):
                  "delta": tuned["delta"] if tuned else None,
                  "blocks": tuned["sssp_blocks"] if tuned else None,
                  "local_rounds": tuned["local_rounds"] if tuned else None,
-                 "autotuned": bool(tuned)},
+                 "label_bits": label_bits, "narrow_reruns": narrow_reruns,
+                 "far_scan": tuned.get("far_scan") if tuned else None,
+                 "autotuned": bool(tuned) and not args.tuned},
         "tree": {"edges": int(res.edges.shape[0]), "total": int(res.total)},
         "graph_load_s": load_s,
         "clocks": clocks,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        ref, times = cpu_oracle_time(g, seeds)
-        same = bool(ref.total == res.total and np.array_equal(ref.edges, res.edges))
-        line["cpu_baseline"] = {"kind": "oracle", "value": len(times) / sum(times),
-                                "unit": "trees/s", "cores": 1,
-                                "sample": f"{len(times)} whole queries of the workload, "
-                                          "single-threaded C oracle",
-                                "matches_gpu": same}
+    if child is not None:
+        ref = finish_oracle_child(child)
+        if "error" in ref:
+            line["cpu_baseline"] = {"kind": "oracle", "value": None, "unit": "trees/s",
+                                    "cores": 1, "error": ref["error"]}
+        else:
+            gpu_sha = hashlib.sha256(np.ascontiguousarray(res.edges, np.uint32)
+                                     .tobytes()).hexdigest()
+            same = bool(ref["total"] == res.total and ref["edges_sha"] == gpu_sha)
+            line["cpu_baseline"] = {"kind": "oracle", "value": 1.0 / ref["seconds"],
+                                    "unit": "trees/s", "cores": 1,
+                                    "sample": "1 whole query of the workload, single-threaded C "
+                                              "oracle (run beside the GPU measurement)",
+                                    "seconds": ref["seconds"], "matches_gpu": same,
+                                    **host_info()}
     print(json.dumps(line), flush=True)
 
 
@@ -645,20 +745,21 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default band width and grid size")
     ap.add_argument("--tuned", default=None,
-                    help="DELTA,BLOCKS,LOCAL_ROUNDS instead of autotuning (BLOCKS 0 = all)")
+                    help="DELTA,BLOCKS,LOCAL_ROUNDS[,LABEL_BITS,FAR_SCAN] instead of autotuning "
+                         "(BLOCKS 0 = all; LABEL_BITS 0/32/64; FAR_SCAN -1/0/1)")
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3],
-                    help="plain mode: single-query workload (2 = the 4096^2 grid, the default; "
-                         "1 = R-MAT 16, 3 = R-MAT 26, use with --no-cpu-baseline)")
+                    help="plain mode: single-query workload (3 = R-MAT 26 with 10,000 seeds, "
+                         "the default; 2 = the 4096^2 grid; 1 = R-MAT 16)")
     ap.add_argument("--batch-scale", type=int, default=None,
                     help="batch mode, profiling only: R-MAT scale instead of 22")
     ap.add_argument("--with-large", action="store_true",
                     help="ablation mode: include the R-MAT scale-26 workload")
     ap.add_argument("--mode", choices=["plain", "batch", "serve", "ablation", "weights", "seeds"],
                     default="plain",
-                    help="plain: the grid single-query workload (default); batch: R-MAT 22 with "
+                    help="plain: the single-query workload (default); batch: R-MAT 22 with "
                          "64 batched queries; serve: R-MAT 24 query stream; ablation: "
                          "relaxation order on the single-query workloads; weights: "
                          "sensitivity to the weight range; seeds: seed-selection strategies")

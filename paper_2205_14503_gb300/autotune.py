@@ -8,11 +8,17 @@ repeated relaxations of hub rows), and the best point depends on the
 graph: a high-diameter grid is latency-bound (local rounds carry the
 wavefront several hops per grid barrier), a scale-free graph is
 throughput-bound (no local rounds, all co-resident blocks, a narrow band
-with the split on).  ``tune`` tries a small grid of both on sample queries, timing
-the Voronoi kernel with the library's own CUDA events, applies the fastest
-and caches it in a JSON file keyed by a fingerprint of the graph and the GPU
-name, so later handles of the same graph start tuned (``apply_cached``).
-Results never depend on these settings, only the time does.
+with the split on).  ``tune`` tries a small grid of both on sample queries,
+timing the whole query (Voronoi phase, bridge scan and tree) with the
+library's own CUDA events; at the best point it then tries the label width
+(32-bit labels halve the random label traffic of scale-free graphs but add
+work to the latency-bound hops of a grid) and how a band split finds the
+vertices left for later bands (a pile of far proposals or a scan of every
+label).  It applies the fastest and caches it in a JSON file keyed by a
+fingerprint of the graph and the GPU name, so later handles of the same
+graph start tuned (``apply_cached``).  Results never depend on these
+settings, only the time does.  Tune on sample queries other than the ones
+to be timed.
 """
 from __future__ import annotations
 
@@ -68,19 +74,37 @@ def apply_cached(G: "st.SteinerGraph", graph, cache_path: str = DEFAULT_CACHE,
     G.set_param("delta", entry["delta"])
     G.set_param("sssp_blocks", min(entry["sssp_blocks"], G.get_param("sssp_max_blocks")))
     G.set_param("local_rounds", entry.get("local_rounds", 0))
+    G.set_param("label_bits", entry.get("label_bits", 0))
+    G.set_param("far_scan", entry.get("far_scan", -1))
     return entry
 
 
-def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.125, 0.25, 0.5, 1, 2),
-         block_fractions=(0.5, 1.0), local_rounds=(0, 32), reps: int = 2,
+def _time(G, sample_seeds, reps):
+    ms = 0.0
+    for _ in range(reps):
+        for seeds in sample_seeds:
+            r = G.query_detail(seeds, pairs=False)
+            if r.status not in (st.STEINER_OK, st.STEINER_EDISCONNECTED):
+                raise st.SteinerError(r.status, st.last_error())
+            ms += sum(r.stats[k] for k in ("ms_init", "ms_voronoi", "ms_bridges", "ms_mst",
+                                           "ms_tree"))
+    return ms / reps
+
+
+def tune(G: "st.SteinerGraph", graph, sample_seeds,
+         delta_factors=(0.0625, 0.125, 0.25, 0.5, 1, 2), block_fractions=(0.5, 1.0),
+         local_rounds=(0, 32), label_bits=(0, 64), far_scan=(0, 1), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
-    """Times the Voronoi kernel over a grid of (delta, blocks, local
-    rounds) on the sample seed sets, applies the fastest and (optionally)
-    caches it."""
+    """Times whole queries over a grid of (delta, blocks, local rounds) on
+    the sample seed sets (label width and split mode automatic), then over
+    (label width, split mode) at the best point; applies the fastest and
+    (optionally) caches it."""
     d0 = G.get_param("delta")
     bmax = G.get_param("sssp_max_blocks")
     sm = max(1, G.get_param("sm_count"))
     trials = []
+    G.set_param("label_bits", 0)
+    G.set_param("far_scan", -1)
     for fb in block_fractions:
         blocks = max(sm, int(round(bmax * fb / sm)) * sm)
         blocks = min(blocks, bmax)
@@ -90,23 +114,28 @@ def tune(G: "st.SteinerGraph", graph, sample_seeds, delta_factors=(0.125, 0.25, 
                 G.set_param("delta", delta)
                 G.set_param("sssp_blocks", blocks)
                 G.set_param("local_rounds", lr)
-                ms = 0.0
-                for _ in range(reps):
-                    for seeds in sample_seeds:
-                        r = G.query_detail(seeds, pairs=False)
-                        if r.status not in (st.STEINER_OK, st.STEINER_EDISCONNECTED):
-                            raise st.SteinerError(r.status, st.last_error())
-                        ms += r.stats["ms_voronoi"]
-                trials.append((ms / reps, delta, blocks, lr))
+                trials.append((_time(G, sample_seeds, reps), delta, blocks, lr, 0, -1))
     trials.sort()
-    best_ms, delta, blocks, lr = trials[0]
+    _, delta, blocks, lr, _, _ = trials[0]
     G.set_param("delta", delta)
     G.set_param("sssp_blocks", blocks)
     G.set_param("local_rounds", lr)
-    entry = {"delta": delta, "sssp_blocks": blocks, "local_rounds": lr, "ms_voronoi": best_ms,
-             "default_delta": d0, "max_blocks": bmax,
-             "trials": [{"ms": t, "delta": d, "blocks": b, "local_rounds": r}
-                        for t, d, b, r in trials]}
+    for lb in label_bits:
+        for fs in far_scan:
+            G.set_param("label_bits", lb)
+            G.set_param("far_scan", fs)
+            trials.append((_time(G, sample_seeds, reps), delta, blocks, lr, lb, fs))
+    trials.sort()
+    best_ms, delta, blocks, lr, lb, fs = trials[0]
+    G.set_param("delta", delta)
+    G.set_param("sssp_blocks", blocks)
+    G.set_param("local_rounds", lr)
+    G.set_param("label_bits", lb)
+    G.set_param("far_scan", fs)
+    entry = {"delta": delta, "sssp_blocks": blocks, "local_rounds": lr, "label_bits": lb,
+             "far_scan": fs, "ms_query": best_ms, "default_delta": d0, "max_blocks": bmax,
+             "trials": [{"ms": t, "delta": d, "blocks": b, "local_rounds": r, "label_bits": x,
+                         "far_scan": y} for t, d, b, r, x, y in trials]}
     if cache_path:
         cache = _load(cache_path)
         cache[_key(graph, device)] = entry

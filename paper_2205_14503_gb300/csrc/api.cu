@@ -342,9 +342,12 @@ int query_locked(steiner_graph *G, const int32_t *seeds, uint32_t k, steiner_res
                     break;
                 }
             double us = t1 > c.trace_ns[i] ? 1e-3 * (double)(t1 - c.trace_ns[i]) : -1.0;
-            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u  %.1f us  relax %llu improved %llu\n",
+            const double nw = (double)(G->geo.sssp_blocks * (G->geo.threads / 32));
+            fprintf(stderr, "[steiner]   it %d: near %u heavy %u far %u T %u  %.1f us  relax %llu "
+                    "improved %llu atomics %llu  warp busy mean %.1f max %.1f us\n",
                     i, c.trace[i][0], c.trace[i][1], c.trace[i][2], c.trace[i][3], us,
-                    c.trace_relax[i][0], c.trace_relax[i][1]);
+                    c.trace_relax[i][0], c.trace_relax[i][1], c.trace_relax[i][2],
+                    1e-3 * (double)c.trace_busy[i][0] / nw, 1e-3 * (double)c.trace_busy[i][1]);
         }
     }
     if (rc == STEINER_OK || rc == STEINER_EDISCONNECTED) {

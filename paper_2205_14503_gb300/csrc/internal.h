@@ -94,7 +94,8 @@ struct Control {
     uint32_t bands;
     uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
     unsigned long long trace_ns[TRACE_LEN];   // their start times (global timer, ns)
-    unsigned long long trace_relax[TRACE_LEN][2];   // relaxations, improvements (when traced)
+    unsigned long long trace_relax[TRACE_LEN][3];   // relaxations, improvements, atomics (traced)
+    unsigned long long trace_busy[TRACE_LEN][2];    // warps' relaxation time: sum, max (ns)
     unsigned long long end_ns;                // end of the last iteration
 };
 

@@ -252,7 +252,8 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                                             const uint64_t (&lab)[ILP], bool precheck,
                                             bool stream, uint32_t wlo, uint32_t whi,
                                             unsigned long long &attempts,
-                                            unsigned long long &improved, bool &narrow_miss) {
+                                            unsigned long long &improved, bool &narrow_miss,
+                                            unsigned long long &atomics) {
     uint2 e[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
@@ -276,6 +277,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                 } else {
                     const uint32_t nl = ((uint32_t)nd[u] << a.lshift) | (uint32_t)lab[u];
                     if (!precheck || nl < ldcg_u32(&a.label32[e[u].x])) {
+                        ++atomics;
                         const uint32_t old = atomicMin(&a.label32[e[u].x], nl);
                         imp[u] = nl < old;
                     }
@@ -284,6 +286,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                 // proposals at or above 2^32 - 1 are skipped; the scan reports the overflow
                 uint64_t nl = (nd[u] << 32) | (lab[u] & 0xFFFFFFFFull);
                 if (!precheck || nl < ldcg_u64(&a.label[e[u].x])) {
+                    ++atomics;
                     uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
                                              (unsigned long long)nl);
                     imp[u] = nl < old;
@@ -377,7 +380,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     Control *ctl = a.ctl;
     unsigned long long attempts = 0, improved = 0;
     bool narrow_miss = false;
-    unsigned long long att0 = 0, imp0 = 0;     // counts at the start of the iteration (trace)
+    unsigned long long att0 = 0, imp0 = 0, atomics = 0, atm0 = 0;   // trace counters
+    unsigned long long t_start = 0;
     uint32_t it = 0, phase = 0, bands = 0;
     uint64_t T = a.delta;
     bool first = (blockIdx.x == 0 && threadIdx.x == 0);
@@ -432,6 +436,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         uint32_t per = (n_light + nwarps - 1) / nwarps;
         uint32_t bsz = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : per <= 8 ? 8 : per <= 16 ? 16 : 32;
         const uint32_t n_work = n_heavy + (n_light + bsz - 1) / bsz;
+        if (a.trace) t_start = global_ns();
         for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
             if (wi < n_heavy) {
                 // one CHUNK of a high-degree vertex per warp
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         labs[q] = lab;
                     }
                     relax_group<NARROW>(a, st, t, valid, arc, labs, true, true, wlo, whi, attempts,
-                                improved, narrow_miss);
+                                improved, narrow_miss, atomics);
                 }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         arc[q] = so + (j - eo);
                     }
                     relax_group<NARROW>(a, st, t, valid, arc, labs, bsz == 32, false, wlo, whi,
-                                attempts, improved, narrow_miss);
+                                attempts, improved, narrow_miss, atomics);
                 }
             }
         }
@@ -554,7 +559,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                             arc[q] = so + (j - eo);
                         }
                         relax_group<NARROW>(a, st, t, valid, arc, labs, false, false, wlo, whi,
-                                    attempts, improved, narrow_miss);
+                                    attempts, improved, narrow_miss, atomics);
                     }
                 }
                 lo = hi;
@@ -562,18 +567,27 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             if (lane == 0) st.local_lo[wib] = lo;
         }
         if (a.trace && it < TRACE_LEN) {
-            unsigned long long da = attempts - att0, di = improved - imp0;
+            // per warp: busy time of this iteration's relaxation (sum, max)
+            const unsigned long long busy = global_ns() - t_start;
+            unsigned long long da = attempts - att0, di = improved - imp0, dm = atomics - atm0;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
                 da += __shfl_xor_sync(FULL, da, o);
                 di += __shfl_xor_sync(FULL, di, o);
+                dm += __shfl_xor_sync(FULL, dm, o);
             }
-            if (lane == 0 && (da | di)) {
-                atomicAdd(&ctl->trace_relax[it][0], da);
-                atomicAdd(&ctl->trace_relax[it][1], di);
+            if (lane == 0) {
+                if (da | di) {
+                    atomicAdd(&ctl->trace_relax[it][0], da);
+                    atomicAdd(&ctl->trace_relax[it][1], di);
+                    atomicAdd(&ctl->trace_relax[it][2], dm);
+                }
+                atomicAdd(&ctl->trace_busy[it][0], busy);
+                atomicMax(&ctl->trace_busy[it][1], busy);
             }
             att0 = attempts;
             imp0 = improved;
+            atm0 = atomics;
         }
         flush_stage(st, t, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {

@@ -26,10 +26,10 @@ def _rank_main(rank: int, world: int, port: int, out):
     w, r, _ = bench.dist_setup()
     bench.barrier(w)
     slowest = bench.max_over_ranks(10.0 * (r + 1), w)
-    g, seeds = bench.workload(r, side=64, k=16)
+    g, seeds, tune_seeds = bench.workload(r, side=64, k=16)
     bench.barrier(w)
     dist.destroy_process_group()
-    out.put((r, w, slowest, g.n, seeds.tolist()))
+    out.put((r, w, slowest, g.n, seeds.tolist(), tune_seeds.tolist()))
 
 
 def test_two_replicas_over_gloo():
@@ -47,12 +47,14 @@ def test_two_replicas_over_gloo():
             if p.is_alive():
                 p.kill()
     assert all(p.exitcode == 0 for p in procs)
-    (r0, w0, m0, n0, s0), (r1, w1, m1, n1, s1) = results
+    (r0, w0, m0, n0, s0, t0), (r1, w1, m1, n1, s1, t1) = results
     assert (r0, r1) == (0, 1) and w0 == w1 == 2
     assert m0 == m1 == 20.0                 # both ranks see the slowest rank's time
     assert n0 == n1 == 64 * 64              # the same graph on every replica
     assert len(s0) == len(s1) == 16 and s0 != s1   # own queries of the same size
     assert len(set(s1)) == 16 and all(0 <= v < n1 for v in s1)
+    # the autotuner's sample is another seed set of the same size
+    assert len(t0) == len(t1) == 16 and t0 != s0 and t1 != s1 and t0 != t1
 
 
 def test_single_process_needs_no_process_group(monkeypatch):
