@@ -511,7 +511,8 @@ def run_batch_mode(args, world, rank, local):
             "config": {"workload": f"rmat{args.batch_scale or 22}_batch64", "n": g.n,
                        "arcs": g.n_arcs, "queries": len(qs),
                        "k_range": [3, 1000],
-                       "tuned": {k: tuned[k] for k in ("delta", "sssp_blocks", "local_rounds")}
+                       "tuned": {k: tuned.get(k) for k in ("delta", "sssp_blocks", "local_rounds",
+                                                            "label_bits", "far_scan")}
                        if tuned else None},
             "plain_queries_per_s": nq / t_plain, "speedup_vs_plain": t_plain / t_batch,
             "identical_to_plain": same, "phase_ms": parts}
@@ -586,7 +587,8 @@ def run_serve_mode(args, world, rank, local):
             "config": {"workload": "rmat24_serve", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
                        "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64,
                        "yield_div": G_yield_div,
-                       "tuned": {k: tuned[k] for k in ("delta", "sssp_blocks", "local_rounds")}
+                       "tuned": {k: tuned.get(k) for k in ("delta", "sssp_blocks", "local_rounds",
+                                                            "label_bits", "far_scan")}
                        if tuned else None},
             "saturated": {"p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
                           "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},

@@ -193,6 +193,44 @@ __device__ __forceinline__ void stage_append(bool want, uint32_t v, uint32_t *bu
     if (g != INF32) gq[g] = v;
 }
 
+// Warp-synchronous append of v (lanes with `want`) to this warp's own
+// region (region[0, *cnt), capacity cap; *cnt is written by this warp
+// only).  If the appends do not fit and `flush` allows it, the warp first
+// moves the region to the global queue (gq, *gcount, capacity gcap) with
+// one atomicAdd and starts the region over; otherwise the lanes that do
+// not fit go to the global queue directly.  All lanes call.
+__device__ __forceinline__ void region_append(bool want, uint32_t v, uint32_t *region,
+                                              uint32_t *cnt, uint32_t cap, bool flush,
+                                              uint32_t *gq, uint32_t *gcount, uint32_t gcap,
+                                              uint32_t *err) {
+    const uint32_t mask = __ballot_sync(FULL, want);
+    if (mask == 0) return;
+    const uint32_t lane = lane_id();
+    uint32_t n = *(volatile uint32_t *)cnt;
+    const uint32_t k = (uint32_t)__popc(mask);
+    if (flush && n + k > cap) {
+        n = min(n, cap);
+        uint32_t base = 0;
+        if (lane == 0 && n) base = atomicAdd(gcount, n);
+        base = __shfl_sync(FULL, base, 0);
+        for (uint32_t i = lane; i < n; i += 32) {
+            const uint32_t slot = base + i;
+            if (slot < gcap) gq[slot] = region[i];
+            else atomicOr(err, ERR_CAPACITY);
+        }
+        __syncwarp();       // the region is read out before it is refilled
+        n = 0;
+    }
+    const uint32_t slot = n + (uint32_t)__popc(mask & lanemask_lt());
+    const bool local = want && slot < cap;
+    if (local) region[slot] = v;
+    const uint32_t g = warp_append(want && !local, gcount, gcap, err);
+    if (g != INF32) gq[g] = v;
+    __syncwarp();
+    if (lane == 0) *(volatile uint32_t *)cnt = n + k;
+    __syncwarp();
+}
+
 // Slot of the seed pair (a, b), a < b < k, in the upper-triangle table:
 // ascending slot order is ascending (a, b) order.
 __host__ __device__ __forceinline__ uint64_t pair_slot(uint64_t a, uint64_t b, uint64_t k) {

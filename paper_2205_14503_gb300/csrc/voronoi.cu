@@ -117,6 +117,8 @@ constexpr uint32_t NEAR_STAGE = 4096;  // block staging capacity (near items)
 constexpr uint32_t SSSP_WARPS = 8;     // warps per block (256 threads)
 constexpr uint32_t NEAR_REGION = NEAR_STAGE / SSSP_WARPS;   // one region per warp
 constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
+constexpr uint32_t BAND_STAGE = 2048;  // block staging capacity (band-list items)
+constexpr uint32_t BAND_REGION = BAND_STAGE / SSSP_WARPS;
 
 // Where the appends of one processing segment go.
 struct PushTargets {
@@ -127,20 +129,28 @@ struct PushTargets {
     uint32_t *farq;      // far pile of the current phase
     uint32_t *far_count;
     uint32_t *far_min;
+    uint32_t *bandq;     // band list and its fill counter
+    uint32_t *band_count;
     uint32_t tag_next;
     uint32_t tag_far;
     uint64_t T;
+    // A full warp region may move to the global queue mid-segment (not
+    // during the warp-local rounds, which index into the region).
+    bool flush;
 };
 
-// Per-block staging buffers: warps append with shared-memory atomics; the
-// block moves them to the global queues with one global atomicAdd each at
-// the end of the segment (flush_stage).  Full buffers spill straight to the
-// global queue.
-// The near buffer has one region per warp: a warp stages its own pushes
-// and, in the local rounds, relaxes them itself.
+// Per-block staging buffers.  Near and band-list appends go to one region
+// per warp, which only that warp touches: a full region moves to the global
+// queue with one global atomicAdd (one per region, not one per append: a
+// single queue counter that every warp bumps on every append serialises the
+// whole grid on one L2 address), and the rest moves at the end of the
+// segment (flush_stage).  In the local rounds a warp relaxes its own near
+// region.  Far appends share one block buffer (shared-memory atomics).
 struct Stage {
     uint32_t near_buf[NEAR_STAGE];
     uint32_t far_buf[FAR_STAGE];
+    uint32_t band_buf[BAND_STAGE];
+    uint32_t band_n[SSSP_WARPS];    // items staged per band region
     uint32_t near_n[SSSP_WARPS];    // items staged per warp region
     uint32_t local_lo[SSSP_WARPS];  // region[0, local_lo) was relaxed by its warp already
     uint32_t near_off[SSSP_WARPS];  // flush: offset of each region's rest
@@ -155,6 +165,7 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
     }
     if (threadIdx.x < SSSP_WARPS) {
         st.near_n[threadIdx.x] = 0;
+        st.band_n[threadIdx.x] = 0;
         st.local_lo[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -179,13 +190,23 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
         if (st.far_min != INF32) atomicMin(t.far_min, st.far_min);
     }
     __syncthreads();
-    {   // each warp moves the rest of its own region
+    {   // each warp moves the rest of its own regions
         const uint32_t w = threadIdx.x >> 5;
         const uint32_t hi = min(st.near_n[w], NEAR_REGION), lo = st.local_lo[w];
         for (uint32_t i = lo + lane_id(); i < hi; i += 32) {
             uint32_t slot = st.base_near + st.near_off[w] + (i - lo);
             if (slot < n) t.qn[slot] = st.near_buf[w * NEAR_REGION + i];
             else atomicOr(err, ERR_CAPACITY);
+        }
+        const uint32_t nb = min(st.band_n[w], BAND_REGION);
+        if (nb) {
+            uint32_t base = 0;
+            if (lane_id() == 0) base = atomicAdd(t.band_count, nb);
+            base = __shfl_sync(FULL, base, 0);
+            for (uint32_t i = lane_id(); i < nb; i += 32) {
+                if (base + i < n) t.bandq[base + i] = st.band_buf[w * BAND_REGION + i];
+                else atomicOr(err, ERR_CAPACITY);
+            }
         }
     }
     for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -201,8 +222,8 @@ __device__ __forceinline__ void push_near(const SsspArgs &a, Stage &st, const Pu
                                           bool want, uint32_t v, uint32_t deg) {
     bool heavy = want && deg >= HEAVY_DEG;
     const uint32_t w = threadIdx.x >> 5;
-    stage_append(want && !heavy, v, st.near_buf + w * NEAR_REGION, &st.near_n[w], NEAR_REGION, t.qn,
-                 t.qn_count, a.n, &a.ctl->err);
+    region_append(want && !heavy, v, st.near_buf + w * NEAR_REGION, &st.near_n[w], NEAR_REGION,
+                  t.flush, t.qn, t.qn_count, a.n, &a.ctl->err);
     if (heavy) {
         uint32_t nc = (deg + CHUNK - 1) / CHUNK;
         uint32_t base = atomicAdd(t.hqn_count, nc);
@@ -330,12 +351,13 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
 // Lists vertex u (lanes with `want`; hdeg arcs in its heavy part) in the
 // current band once: as one item, or as CHUNK-arc pieces when the heavy
 // part is long.  A vertex without heavy arcs needs no listing.
-__device__ __forceinline__ void band_track(const SsspArgs &a, bool want, uint32_t u, uint32_t hdeg,
-                                           uint32_t tag) {
+__device__ __forceinline__ void band_track(const SsspArgs &a, Stage &st, bool want, uint32_t u,
+                                           uint32_t hdeg, uint32_t tag) {
     bool add = want && hdeg > 0 && atomicExch(&a.stamp_band[u], tag) != tag;
     const bool big = add && hdeg >= HEAVY_DEG;
-    uint32_t slot = warp_append(add && !big, &a.ctl->band_count, a.n, &a.ctl->err);
-    if (slot != INF32) a.band_q[slot] = u;
+    const uint32_t w = threadIdx.x >> 5;
+    region_append(add && !big, u, st.band_buf + w * BAND_REGION, &st.band_n[w], BAND_REGION, true,
+                  a.band_q, &a.ctl->band_count, a.n, &a.ctl->err);
     if (big) {
         const uint32_t nc = (hdeg + CHUNK - 1) / CHUNK;
         const uint32_t base = atomicAdd(&a.ctl->band_hcount, nc);
@@ -421,9 +443,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         t.farq = fc ? a.far1 : a.far0;
         t.far_count = &ctl->far_count[fc];
         t.far_min = &ctl->far_min[fc];
+        t.bandq = a.band_q;
+        t.band_count = &ctl->band_count;
         t.tag_next = a.base_near + it + 1;
         t.tag_far = a.base_far + phase;
         t.T = T;
+        t.flush = true;
         // arcs relaxed by this iteration: all; light ones while a band
         // iterates under the split; heavy ones in the band's closing pass
         const uint32_t wlo = hp ? a.delta : 0u;
@@ -484,7 +509,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                     lab = sssp_label<NARROW>(a, u);
                     if (lab == INF64) deg = 0;
                 }
-                if (track) band_track(a, has, u, hdeg, tag_band);
+                if (track) band_track(a, st, has, u, hdeg, tag_band);
                 uint32_t incl = warp_inclusive_scan(deg);
                 uint32_t excl = incl - deg;
                 uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -516,6 +541,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             // itself, a hop per round, with no block barrier between hops.
             const uint32_t wib = threadIdx.x >> 5;
             const uint32_t tag_cur = t.tag_next - 1;
+            t.flush = false;            // the loop below indexes into the region
             uint32_t *region = st.near_buf + wib * NEAR_REGION;
             uint32_t lo = 0;
             for (uint32_t r = 0; r < a.local_rounds; ++r) {
@@ -540,7 +566,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         hdeg = a.lend ? r1 - le : r1 - s;
                         lab = sssp_label<NARROW>(a, u);
                     }
-                    if (track) band_track(a, has, u, hdeg, tag_band);
+                    if (track) band_track(a, st, has, u, hdeg, tag_band);
                     uint32_t incl = warp_inclusive_scan(deg);
                     uint32_t excl = incl - deg;
                     uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -655,9 +681,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.farq = fc ? a.far0 : a.far1;
         u.far_count = &ctl->far_count[fc ^ 1];
         u.far_min = &ctl->far_min[fc ^ 1];
+        u.bandq = a.band_q;
+        u.band_count = &ctl->band_count;
         u.tag_next = a.base_near + its;
         u.tag_far = a.base_far + phase;
         u.T = T;
+        u.flush = true;
         // the far pile, or with the far scan every vertex (coalesced labels)
         const uint32_t n_split = a.far_scan ? a.n : nf;
         for (uint32_t b = warp * 32; b < n_split; b += nwarps * 32) {
