@@ -28,11 +28,8 @@ namespace stn {
 // bound by the latency of each item's chain of L2 round trips, so more
 // resident warps pay more than more pairs per warp.
 constexpr int MQ_ILP = 2;
-// Per-block staging, one region per warp (see region_append): a full region
-// moves to the global queue with one atomicAdd instead of one per append.
-constexpr uint32_t MQ_NEAR_STAGE = 2048;
-constexpr uint32_t MQ_FAR_STAGE = 1024;
-constexpr uint32_t MQ_BAND_STAGE = 1024;
+constexpr uint32_t MQ_NEAR_STAGE = 1024;
+constexpr uint32_t MQ_FAR_STAGE = 512;
 
 struct MqArgs {
     const uint32_t *__restrict__ row_ptr;
@@ -66,9 +63,6 @@ __device__ __forceinline__ uint32_t *band_list(const MqArgs &a, uint32_t i) {
 
 constexpr int MQ_WARPS = 256 / 32;
 constexpr int MQ_MAX_BLOCKS = 1024;
-constexpr uint32_t MQ_NEAR_REGION = MQ_NEAR_STAGE / MQ_WARPS;
-constexpr uint32_t MQ_FAR_REGION = MQ_FAR_STAGE / MQ_WARPS;
-constexpr uint32_t MQ_BAND_REGION = MQ_BAND_STAGE / MQ_WARPS;
 
 struct MqStage {
     uint64_t boff[MQ_MAX_BLOCKS];          // pair offset of each block's frontier segment
@@ -76,10 +70,7 @@ struct MqStage {
     uint64_t carry, W;
     uint32_t near_buf[MQ_NEAR_STAGE];
     uint32_t far_buf[MQ_FAR_STAGE];
-    uint32_t band_buf[MQ_BAND_STAGE];
-    uint32_t near_n[MQ_WARPS], far_n[MQ_WARPS], band_n[MQ_WARPS];   // per warp region
-    uint32_t near_off[MQ_WARPS], far_off[MQ_WARPS];
-    uint32_t base_near, base_far;
+    uint32_t near_n, far_n, base_near, base_far;
     unsigned long long act;
     unsigned long long T[MQ_SLOTS];        // current thresholds (block copy)
     unsigned long long Tnew[MQ_SLOTS];     // thresholds after a split
@@ -154,10 +145,10 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
 }
 
 __device__ __forceinline__ void seg_reset(MqStage &st) {
-    if (threadIdx.x == 0) st.act = 0;
-    if (threadIdx.x < MQ_WARPS) {
-        st.near_n[threadIdx.x] = 0;
-        st.far_n[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        st.near_n = 0;
+        st.far_n = 0;
+        st.act = 0;
     }
     if (threadIdx.x < MQ_SLOTS) {
         st.fmin[threadIdx.x] = INF32;
@@ -169,14 +160,8 @@ __device__ __forceinline__ void seg_reset(MqStage &st) {
 __device__ __forceinline__ void seg_flush(MqStage &st, const MqTargets &t, MqControl *ctl,
                                           uint32_t n) {
     __syncthreads();
+    uint32_t nn = min(st.near_n, MQ_NEAR_STAGE), nf = min(st.far_n, MQ_FAR_STAGE);
     if (threadIdx.x == 0) {
-        uint32_t nn = 0, nf = 0;
-        for (uint32_t w = 0; w < MQ_WARPS; ++w) {
-            st.near_off[w] = nn;
-            st.far_off[w] = nf;
-            nn += min(st.near_n[w], MQ_NEAR_REGION);
-            nf += min(st.far_n[w], MQ_FAR_REGION);
-        }
         st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
         st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
         if (st.act) atomicOr(t.act, st.act);
@@ -187,35 +172,24 @@ __device__ __forceinline__ void seg_flush(MqStage &st, const MqTargets &t, MqCon
         if (st.fpend[q]) atomicAdd(&ctl->far_pending[q], st.fpend[q]);
     }
     __syncthreads();
-    const uint32_t w = threadIdx.x >> 5;
-    const uint32_t nn = min(st.near_n[w], MQ_NEAR_REGION), nf = min(st.far_n[w], MQ_FAR_REGION);
-    for (uint32_t i = lane_id(); i < nn; i += 32) {
-        uint32_t slot = st.base_near + st.near_off[w] + i;
-        if (slot < n) t.qn[slot] = st.near_buf[w * MQ_NEAR_REGION + i];
+    for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        uint32_t slot = st.base_near + i;
+        if (slot < n) t.qn[slot] = st.near_buf[i];
         else atomicOr(&ctl->err, ERR_CAPACITY);
     }
-    for (uint32_t i = lane_id(); i < nf; i += 32) {
-        uint32_t slot = st.base_far + st.far_off[w] + i;
-        if (slot < n) t.farq[slot] = st.far_buf[w * MQ_FAR_REGION + i];
+    for (uint32_t i = threadIdx.x; i < nf; i += blockDim.x) {
+        uint32_t slot = st.base_far + i;
+        if (slot < n) t.farq[slot] = st.far_buf[i];
         else atomicOr(&ctl->err, ERR_CAPACITY);
     }
-}
-
-// Far appends through this warp's far region.
-__device__ __forceinline__ void mq_push_far(const MqArgs &a, MqStage &st, const MqTargets &t,
-                                            bool want, uint32_t v) {
-    const uint32_t w = threadIdx.x >> 5;
-    region_append(want, v, st.far_buf + w * MQ_FAR_REGION, &st.far_n[w], MQ_FAR_REGION, true,
-                  t.farq, t.far_count, a.n, &a.ctl->err);
 }
 
 // A vertex with near work joins the next frontier through the staging
 // buffer.  (Hubs need no special handling: work is split by pairs.)
 __device__ __forceinline__ void mq_push_near(const MqArgs &a, MqStage &st, const MqTargets &t,
                                              bool want, uint32_t v) {
-    const uint32_t w = threadIdx.x >> 5;
-    region_append(want, v, st.near_buf + w * MQ_NEAR_REGION, &st.near_n[w], MQ_NEAR_REGION, true,
-                  t.qn, t.qn_count, a.n, &a.ctl->err);
+    stage_append(want, v, st.near_buf, &st.near_n, MQ_NEAR_STAGE, t.qn, t.qn_count, a.n,
+                 &a.ctl->err);
 }
 
 // Relaxes up to MQ_ILP (arc, slot) pairs per lane.
@@ -288,7 +262,8 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
 #pragma unroll
     for (int i = 0; i < MQ_ILP; ++i) {
         mq_push_near(a, st, t, to_near[i], e[i].x);
-        mq_push_far(a, st, t, to_far[i], e[i].x);
+        stage_append(to_far[i], e[i].x, st.far_buf, &st.far_n, MQ_FAR_STAGE, t.farq, t.far_count,
+                     a.n, &a.ctl->err);
     }
 }
 
@@ -345,7 +320,6 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
         const uint32_t seg_lo = min(n_all, blockIdx.x * seg);
         const uint32_t seg_hi = min(n_all, seg_lo + seg);
         if (threadIdx.x == 0) st.carry = 0;
-        if (threadIdx.x < MQ_WARPS) st.band_n[threadIdx.x] = 0;
         __syncthreads();
         for (uint32_t b0 = seg_lo; b0 < seg_hi; b0 += blockDim.x) {
             uint32_t i = b0 + threadIdx.x;
@@ -372,27 +346,13 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                 const uint32_t deg = i < n_items ? le - r0 : (a.lend ? r1 - le : r1 - r0);
                 w = (uint64_t)deg * (uint64_t)popc64(M);
             }
-            region_append(listed, u, st.band_buf + (threadIdx.x >> 5) * MQ_BAND_REGION,
-                          &st.band_n[threadIdx.x >> 5], MQ_BAND_REGION, true, bln,
-                          &ctl->bcount[tgt], a.n, &ctl->err);
+            const uint32_t ls = warp_append(listed, &ctl->bcount[tgt], a.n, &ctl->err);
+            if (ls != INF32) bln[ls] = u;
             uint64_t incl = block_inclusive_scan64(w, st.wtot);
             if (i < seg_hi) a.item_pre[i] = st.carry + incl - w;
             __syncthreads();
             if (threadIdx.x == blockDim.x - 1) st.carry += incl;
             __syncthreads();
-        }
-        {   // the rest of this warp's band-list region
-            const uint32_t w = threadIdx.x >> 5;
-            const uint32_t nb = min(st.band_n[w], MQ_BAND_REGION);
-            if (nb) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(&ctl->bcount[tgt], nb);
-                base = __shfl_sync(FULL, base, 0);
-                for (uint32_t i = lane; i < nb; i += 32) {
-                    if (base + i < a.n) bln[base + i] = st.band_buf[w * MQ_BAND_REGION + i];
-                    else atomicOr(&ctl->err, ERR_CAPACITY);
-                }
-            }
         }
         if (threadIdx.x == 0) a.bsum[blockIdx.x] = st.carry;
         unsigned long long tm1 = first ? gtimer() : 0;
@@ -649,7 +609,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
             bool keep = valid && (M & ~cleared) != 0;
             if (valid && !keep) a.in_far[v] = 0;
             mq_push_near(a, st, u, to_near, v);
-            mq_push_far(a, st, u, keep, v);
+            stage_append(keep, v, st.far_buf, &st.far_n, MQ_FAR_STAGE, u.farq, u.far_count, a.n,
+                         &ctl->err);
         }
         seg_flush(st, u, ctl, a.n);
         if (!grid_sync(&ctl->bar, &ctl->err)) { reason = 5; break; }

@@ -380,3 +380,31 @@ def test_band_split_by_pile_or_scan(far_scan, delta, local):
         pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
         seeds = wl.sample_distinct(pool, k, 50 + k)
         _compare_forced(g, seeds, far_scan=far_scan, delta=delta, local_rounds=local)
+
+
+@pytest.mark.parametrize("wmax", [10_000, 100_000])
+@pytest.mark.parametrize("mode", ["tuned", "frontier"])
+def test_wide_weight_ranges(wmax, mode):
+    """The weight-range study's wide ranges (weights uniform in [1, 10^4]
+    and [1, 10^5] on R-MAT): cells, distances, preds, the distance graph
+    and the tree equal the oracle's, at a band width scaled to the weights
+    (with the light/heavy split) and as a plain frontier (one unbounded
+    band)."""
+    g = wl.rmat(15, 16, wmax=wmax, seed=61 + wmax % 97)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 48, 62)
+    delta = max(1, wmax // 8) if mode == "tuned" else 0x7FFFFFFF
+    _compare_forced(g, seeds, delta=delta)
+
+
+@pytest.mark.parametrize("strategy", ["bfs_level", "eccentric", "proximate"])
+def test_seed_selection_strategies(strategy):
+    """The seed-selection study's strategies (BFS-level, eccentric and
+    proximate k-BFS seeds) as inputs to the CUDA path, against the oracle
+    element by element, on an R-MAT graph and a grid."""
+    for g, lcc in ((wl.rmat(14, 16, wmax=1000, seed=71), True),
+                   (wl.grid(96, 80, 1000, seed=72), False)):
+        pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
+        make = {"bfs_level": wl.seeds_bfs_level, "eccentric": wl.seeds_eccentric,
+                "proximate": wl.seeds_proximate}[strategy]
+        seeds = make(g, pool, 40, 73)
+        _compare_forced(g, seeds)
