@@ -187,6 +187,17 @@ def workload(rank: int, side: int | None = None, k: int | None = None, cfg: int 
     return g, seeds, tune_seeds
 
 
+def heldout_queries(g, cfg: int, count: int, pool=None):
+    """``count`` seed sets drawn like workload ``cfg``'s query stream but
+    with other salts: the autotuner's sample, never the timed queries."""
+    import paper_2205_14503_gb300.workloads as wl
+    c = wl.CONFIGS[cfg]
+    pool = wl.largest_cc(g) if pool is None else pool
+    base = wl.CONFIG_SEED + cfg + TUNE_SALT
+    ks = wl.log_uniform_sizes(count, c["klo"], c["khi"], base ^ 0x517E)
+    return [wl.sample_distinct(pool, int(k), base + 7919 * i) for i, k in enumerate(ks)]
+
+
 def host_info() -> dict:
     ram = None
     try:
@@ -389,6 +400,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t_start, world)
     barrier(world)
+    label_bits = G.get_param("label_bits_last")      # the width the timed queries used
+    narrow_reruns = G.get_param("narrow_reruns")
     G.close()
 
     if rank != 0:
@@ -399,10 +412,8 @@ def run_ours(args, world, rank, local):
     sssp_ms = statistics.mean(phase["ms_voronoi"])
     # per SSSP launch (one query): every arc record (8 B) and the head's
     # label once, every row offset and label once; labels are 4 or 8 bytes
-    label_bits = G.get_param("label_bits_last")
     lb = label_bits // 8
     alg_bytes = (8 + lb) * m_arcs + (4 + lb) * n
-    narrow_reruns = G.get_param("narrow_reruns")
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (sssp_ms / 1e3) / 1e9
     cfgd = config_dict(g, seeds, args.workload, args.side)
@@ -483,12 +494,14 @@ def run_batch_mode(args, world, rank, local):
         pool = wl.largest_cc(g)
         qs = [wl.sample_distinct(pool, q.size, 0x5EED + 4000 + 97 * rank + i) for i, q in enumerate(qs)]
     G = st.SteinerGraph(g, device=local)
-    tuned = None
+    tuned = btuned = None
     if not args.no_autotune:
-        # set-up, untimed: the graph's band width and grid size, used by both
-        # the plain comparator and the batched engine
+        # set-up, untimed, on held-out queries: the graph's single-query
+        # settings (the plain comparator) and the batched engine's band width
         from paper_2205_14503_gb300 import autotune
-        tuned = autotune.tune(G, g, qs[:2], cache_path=None, device=local)
+        tq = heldout_queries(g, 4, len(qs))
+        tuned = autotune.tune(G, g, tq[:2], cache_path=None, device=local)
+        btuned = autotune.tune_batch(G, g, tq)
     for _ in range(max(args.warmup, 3)):
         G.query_batch(qs)
     plain = [G.query(q) for q in qs]
@@ -522,6 +535,7 @@ def run_batch_mode(args, world, rank, local):
                        "tuned": {k: tuned.get(k) for k in ("delta", "sssp_blocks", "local_rounds",
                                                             "label_bits", "far_scan")}
                        if tuned else None},
+            "batch_delta": (btuned or {}).get("batch_delta"),
             "plain_queries_per_s": nq / t_plain, "speedup_vs_plain": t_plain / t_batch,
             "identical_to_plain": same, "phase_ms": parts}
     print(json.dumps(line), flush=True)
@@ -541,10 +555,13 @@ def run_serve_mode(args, world, rank, local):
     qs = wl.config_seed_sets(5, g)[: args.queries]
     G = st.SteinerGraph(g, device=local)
     h = G.handle
-    tuned = None
+    tuned = btuned = None
     if not args.no_autotune:
+        # set-up, untimed, on held-out queries of the same recipe
         from paper_2205_14503_gb300 import autotune
-        tuned = autotune.tune(G, g, qs[:2], cache_path=None, device=local)
+        tq = heldout_queries(g, 5, 64)
+        tuned = autotune.tune(G, g, tq[:2], cache_path=None, device=local)
+        btuned = autotune.tune_batch(G, g, tq)
 
     def stream(arrivals):
         st.steiner_serve_start(h, 64, 40 << 30)
@@ -595,6 +612,7 @@ def run_serve_mode(args, world, rank, local):
             "config": {"workload": "rmat24_serve", "n": g.n, "arcs": g.n_arcs, "queries": len(qs),
                        "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64,
                        "yield_div": G_yield_div,
+                       "batch_delta": (btuned or {}).get("batch_delta"),
                        "tuned": {k: tuned.get(k) for k in ("delta", "sssp_blocks", "local_rounds",
                                                             "label_bits", "far_scan")}
                        if tuned else None},

@@ -207,6 +207,9 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  just queued, a hop per round, before the grid barrier
  *   "batch_delta"  band width of the multi-query engine (0 = w_max / 8 when
  *                  "delta" is at most the largest weight w_max, else "delta")
+ *   "batch_tails"  1 (default): the tails (MST, expansion, sorted edges) of
+ *                  the queries that finish together run as one launch per
+ *                  step for all of them; 0: one query at a time
  *   "batch_yield_div"  a serving launch returns to the host (to retire and
  *                  admit) once 1/batch_yield_div of its in-flight queries
  *                  converged (1..64, default 1: whole waves), or earlier
@@ -228,8 +231,9 @@ int steiner_serve_stop(steiner_graph_t g);
  * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
  * microseconds, "batch_launches", "batch_iterations", "batch_items",
  * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds, "batch_admitted"
- * (queries admitted into slots) and "batch_admitted_busy" (of those, the
- * ones admitted while other slots were still on the device); "batch_reset"
+ * (queries admitted into slots), "batch_admitted_busy" (of those, the
+ * ones admitted while other slots were still on the device) and
+ * "batch_tail_batches" (retirements whose tails ran batched); "batch_reset"
  * clears the timers and counters).  It returns -1 for an unknown key.
  */
 int steiner_set_param(steiner_graph_t g, const char *key, int64_t value);

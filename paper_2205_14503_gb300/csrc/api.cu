@@ -753,6 +753,20 @@ int api_sorted_seeds(steiner_graph *G, const int32_t *seeds, uint32_t k, std::ve
 
 cudaStream_t api_stream(steiner_graph *G) { return G->stream; }
 
+uint32_t api_reserve_mark_tags(steiner_graph *G, uint32_t count, uint32_t **mark) {
+    *mark = nullptr;
+    if (ensure_n_workspace(G) != STEINER_OK) return 0;
+    Workspace &ws = G->ws;
+    if ((uint64_t)ws.epoch_mark + count > 0x7FFFFFFFull) {
+        if (cudaMemsetAsync(ws.mark, 0, (size_t)ws.n * 4, G->stream) != cudaSuccess) return 0;
+        ws.epoch_mark = 1;
+    }
+    const uint32_t tag0 = ws.epoch_mark;
+    ws.epoch_mark += count;
+    *mark = ws.mark;
+    return tag0;
+}
+
 std::mutex &api_mutex(steiner_graph *G) { return G->mu; }
 const DevGraph &api_graph(steiner_graph *G) { return G->g; }
 int api_device(steiner_graph *G) { return G->device; }

@@ -187,21 +187,6 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(uint32_t *tile_cnt, uin
     if (threadIdx.x == 0) *n_pairs = carry;
 }
 
-// rank pair (a, b) of a table slot: largest a with row start R(a) <= slot
-__device__ __forceinline__ void slot_to_pair(uint64_t slot, uint32_t k, uint32_t &ra,
-                                             uint32_t &rb) {
-    double kk = 2.0 * k - 1.0;
-    double disc = kk * kk - 8.0 * (double)slot;
-    int64_t a = (int64_t)floor((kk - sqrt(disc > 0 ? disc : 0)) * 0.5);
-    if (a < 0) a = 0;
-    if (a > (int64_t)k - 2) a = (int64_t)k - 2;
-    auto row_start = [k](int64_t x) { return (uint64_t)(x * (2 * (int64_t)k - x - 1) / 2); };
-    while (a > 0 && row_start(a) > slot) --a;
-    while (a + 1 <= (int64_t)k - 2 && row_start(a + 1) <= slot) ++a;
-    ra = (uint32_t)a;
-    rb = (uint32_t)(slot - row_start(a) + (uint64_t)a + 1);
-}
-
 __global__ void __launch_bounds__(CT_THREADS) pair_write_kernel(
     const uint64_t *__restrict__ tab, uint64_t slots, uint32_t k,
     const uint32_t *__restrict__ tile_off, uint64_t *e_key, uint32_t *e_ra, uint32_t *e_rb,

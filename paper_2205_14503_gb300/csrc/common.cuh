@@ -237,4 +237,19 @@ __host__ __device__ __forceinline__ uint64_t pair_slot(uint64_t a, uint64_t b, u
     return a * k - a * (a + 1) / 2 + (b - a - 1);
 }
 
+// rank pair (a, b) of a table slot: largest a with row start R(a) <= slot
+__device__ __forceinline__ void slot_to_pair(uint64_t slot, uint32_t k, uint32_t &ra,
+                                             uint32_t &rb) {
+    double kk = 2.0 * k - 1.0;
+    double disc = kk * kk - 8.0 * (double)slot;
+    int64_t a = (int64_t)floor((kk - sqrt(disc > 0 ? disc : 0)) * 0.5);
+    if (a < 0) a = 0;
+    if (a > (int64_t)k - 2) a = (int64_t)k - 2;
+    auto row_start = [k](int64_t x) { return (uint64_t)(x * (2 * (int64_t)k - x - 1) / 2); };
+    while (a > 0 && row_start(a) > slot) --a;
+    while (a + 1 <= (int64_t)k - 2 && row_start(a + 1) <= slot) ++a;
+    ra = (uint32_t)a;
+    rb = (uint32_t)(slot - row_start(a) + (uint64_t)a + 1);
+}
+
 }  // namespace stn

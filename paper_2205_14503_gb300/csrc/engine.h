@@ -35,5 +35,9 @@ int api_run_tail(steiner_graph *G, uint64_t *pairtab, uint32_t *pred_base, uint3
                  uint32_t k, bool overflow, steiner_result_t *out);
 int api_sorted_seeds(steiner_graph *G, const int32_t *seeds, uint32_t k, std::vector<int32_t> &out);
 cudaStream_t api_stream(steiner_graph *G);
+// Reserves `count` consecutive tree-walk tags of the graph's mark array
+// (clearing it when the tags would run out); returns the first tag and the
+// array, or a null array when the workspace cannot be set up.
+uint32_t api_reserve_mark_tags(steiner_graph *G, uint32_t count, uint32_t **mark);
 
 }  // namespace stn

@@ -186,6 +186,9 @@ cudaError_t launch_mst(Workspace &ws, uint32_t k, const Geometry &geo, cudaStrea
 cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t tag,
                         uint32_t n_bits, cudaStream_t s);
 int mst_occupancy(int threads);
+cudaError_t launch_sort_keys(uint64_t *key0, uint64_t *key1, uint32_t *w0, uint32_t *w1,
+                             uint32_t *blk_hist, uint32_t cap, uint32_t key_bits, Control *ctl,
+                             cudaStream_t s);
 
 // graph.cu
 // Builds g.adj_w / g.lend for band width delta (both allocated by the caller).

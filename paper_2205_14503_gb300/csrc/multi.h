@@ -10,7 +10,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/steiner.h"
 #include "internal.h"
+
+struct steiner_graph;
 
 namespace stn {
 
@@ -74,6 +77,54 @@ struct MqState {
     uint32_t seeds_cap[MQ_SLOTS] = {};
     uint32_t base_near = 1;                 // stamp tags are base_near + it
 };
+
+// Batched tails (tails.cu): one retiring slot, and its results.
+struct TailSlot {
+    const uint64_t *pairtab;     // its pair table, k (k - 1) / 2 entries
+    uint64_t n_slots;
+    uint64_t tile0;              // first tile of its table in the global tile numbering
+    uint32_t k;
+    uint32_t q;                  // engine slot: its pred column
+    uint32_t comp0;              // first of its k MST scratch entries
+    uint32_t pad;
+};
+
+struct TailOut {
+    uint32_t pair0, n_pairs;     // its segment of the concatenated pair list
+    uint32_t n_mst;              // MST pairs
+    uint32_t n_edges;            // distinct tree edges
+    unsigned long long total;    // D(G_S)
+};
+
+// Device workspace of the batched tails, grown on demand.
+struct TailWs {
+    TailSlot *d_slots = nullptr, *h_slots = nullptr;
+    TailOut *d_out = nullptr, *h_out = nullptr;
+    Control *ctl = nullptr, *h_ctl = nullptr;
+    uint32_t *tile_cnt = nullptr;
+    uint64_t tile_cap = 0;
+    uint64_t *e_key = nullptr;
+    uint32_t *e_ra = nullptr, *e_rb = nullptr, *e_arc = nullptr, *e_mst = nullptr,
+             *e_owner = nullptr;
+    uint64_t e_cap = 0;
+    uint32_t *comp = nullptr, *hook = nullptr;
+    unsigned long long *best = nullptr;
+    uint64_t comp_cap = 0;
+    uint64_t *key0 = nullptr, *key1 = nullptr;
+    uint32_t *w0 = nullptr, *w1 = nullptr;
+    uint64_t key_cap = 0;
+    uint64_t tree_cap = 0;       // edges the walkers may emit before a fallback
+    uint32_t *hist = nullptr;
+};
+
+void tail_ws_free(TailWs &t);
+// Steps 3-7 of Algorithm 2 for r retiring slots (engine slots qs[i], seed
+// counts ks[i] >= 2, pred columns and pair tables in m) with one launch per
+// step.  Fills res[i] (edges allocated with malloc) and returns STEINER_OK;
+// on a buffer shortfall returns STEINER_ENOMEM with no results, and the
+// caller runs those slots one at a time.
+int run_batched_tails(steiner_graph *G, MqState &m, TailWs &t, const int *qs, const uint32_t *ks,
+                      int r, steiner_result_t *res);
 
 cudaError_t mq_alloc(const DevGraph &g, MqState &m, cudaStream_t s);
 void mq_free(MqState &m);

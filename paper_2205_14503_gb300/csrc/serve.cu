@@ -68,12 +68,18 @@ struct BatchEngine {
     // serves many slots and one retirement scan covers many queries;
     // larger divisors retire earlier, in smaller groups.
     uint32_t yield_div = 1;
+    // Retiring slots' tails (Steps 3-7) in one launch per step for all of
+    // them (1, the default) or slot by slot through the single-query
+    // kernels (0; also the fallback when the batched buffers fall short).
+    uint32_t batched_tails = 1;
+    TailWs tails;
     // cumulative wall time (ms) and counters, for tracing
     double ms_sssp = 0, ms_scan = 0, ms_tail = 0, ms_admit = 0;
     uint64_t launches = 0, relax_attempts = 0, iterations_run = 0;
     // admissions, and those made while other slots were on the device
     // (continuous batching: a query joins a running batch)
     uint64_t admitted = 0, admitted_busy = 0;
+    uint64_t tail_batches = 0;          // retirements whose tails ran batched
     std::atomic<int> free_slots{MQ_SLOTS};
 
     int init() {
@@ -102,6 +108,7 @@ struct BatchEngine {
 
     void release() {
         mq_free(m);                      // also after a partial mq_alloc
+        tail_ws_free(tails);
         if (doorbell_host) cudaFreeHost(doorbell_host);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (h_masks) cudaFreeHost(h_masks);
@@ -278,12 +285,30 @@ struct BatchEngine {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         double t1 = now_s();
         ms_scan += 1e3 * (t1 - t0);
+        // slots without overflow: their tails all at once
+        int bq[MQ_SLOTS];
+        uint32_t bk[MQ_SLOTS];
+        int nb = 0;
+        if (e == cudaSuccess && batched_tails)
+            for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+                const int q = __builtin_ctzll(mm);
+                if (!((h_ctl->slot_overflow >> q) & 1ull) && slots[q].k > 1) {
+                    bq[nb] = q;
+                    bk[nb++] = slots[q].k;
+                }
+            }
+        steiner_result_t bres[MQ_SLOTS];
+        const bool batched = nb > 0 && run_batched_tails(G, m, tails, bq, bk, nb, bres) == STEINER_OK;
+        if (batched) ++tail_batches;
+        int bi = 0;
         for (unsigned long long mm = mask; mm; mm &= mm - 1) {
             int q = __builtin_ctzll(mm);
             steiner_result_t r{};
             if (e != cudaSuccess) {
                 r.status = STEINER_ECUDA;
                 api_set_error(std::string("batched scan: ") + cudaGetErrorString(e));
+            } else if (batched && bi < nb && bq[bi] == q) {
+                r = bres[bi++];
             } else {
                 bool ovf = (h_ctl->slot_overflow >> q) & 1ull;
                 api_run_tail(G, m.pairtab[q], m.pred + q, MQ_SLOTS, slots[q].k, ovf, &r);
@@ -346,6 +371,8 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_relax_attempts") return (int64_t)B->relax_attempts;
     if (k == "batch_admitted") return (int64_t)B->admitted;
     if (k == "batch_admitted_busy") return (int64_t)B->admitted_busy;
+    if (k == "batch_tails") return B->batched_tails;
+    if (k == "batch_tail_batches") return (int64_t)B->tail_batches;
     if (k == "batch_delta") return B->cur_delta();
     if (k == "batch_yield_div") return B->yield_div;
     if (k.rfind("batch_t", 0) == 0 && k.size() == 8 && B->h_ctl) return (int64_t)B->h_ctl->t_part[k[7] - '0'];
@@ -354,7 +381,7 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_reset") {
         B->ms_sssp = B->ms_scan = B->ms_tail = B->ms_admit = 0;
         B->launches = B->iterations_run = 0;
-        B->admitted = B->admitted_busy = 0;
+        B->admitted = B->admitted_busy = B->tail_batches = 0;
         return 0;
     }
     return -1;
@@ -379,6 +406,14 @@ int batch_set_param(steiner_graph *G, const char *key, int64_t value) {
             return STEINER_EINVAL;
         }
         B->batch_delta = (uint32_t)value;
+        return STEINER_OK;
+    }
+    if (k == "batch_tails") {
+        if (value != 0 && value != 1) {
+            api_set_error("batch_tails must be 0 or 1");
+            return STEINER_EINVAL;
+        }
+        B->batched_tails = (uint32_t)value;
         return STEINER_OK;
     }
     if (k == "batch_yield_div") {

@@ -367,3 +367,35 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
 }
 
 }  // namespace stn
+
+namespace stn {
+
+// Sorts N = min(ctl->n_tree, cap) (key, weight) pairs by the low key_bits
+// bits of the key (the result lands back in key0 / w0); blk_hist needs
+// 64 * 256 entries.  Also adds the weights into ctl->total.
+cudaError_t launch_sort_keys(uint64_t *key0, uint64_t *key1, uint32_t *w0, uint32_t *w1,
+                             uint32_t *blk_hist, uint32_t cap, uint32_t key_bits, Control *ctl,
+                             cudaStream_t s) {
+    if (sort_blocks_cache < 0) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, radix_sort_kernel, RS_THREADS, 0);
+        sort_blocks_cache = std::max(1, std::min(nb * current_sm_count(), 64));
+    }
+    SortArgs a;
+    a.key0 = key0;
+    a.key1 = key1;
+    a.w0 = w0;
+    a.w1 = w1;
+    a.blk_hist = blk_hist;
+    a.passes = (key_bits + 7) / 8;
+    if (a.passes & 1) a.passes += 1;
+    a.cap = cap;
+    a.ctl = ctl;
+    cudaError_t e = cudaMemsetAsync(&ctl->bar2, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)radix_sort_kernel, dim3(sort_blocks_cache),
+                                       dim3(RS_THREADS), args, 0, s);
+}
+
+}  // namespace stn

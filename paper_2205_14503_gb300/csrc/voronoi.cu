@@ -119,6 +119,7 @@ constexpr uint32_t NEAR_REGION = NEAR_STAGE / SSSP_WARPS;   // one region per wa
 constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
 constexpr uint32_t BAND_STAGE = 2048;  // block staging capacity (band-list items)
 constexpr uint32_t BAND_REGION = BAND_STAGE / SSSP_WARPS;
+constexpr int SPLIT_ILP = 4;           // 32-vertex chunks per warp step in a band split
 
 // Where the appends of one processing segment go.
 struct PushTargets {
@@ -689,27 +690,44 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.flush = true;
         // the far pile, or with the far scan every vertex (coalesced labels)
         const uint32_t n_split = a.far_scan ? a.n : nf;
-        for (uint32_t b = warp * 32; b < n_split; b += nwarps * 32) {
-            uint32_t i = b + lane;
-            bool valid = i < n_split;
-            uint32_t v = 0, deg = 0;
-            uint64_t d = INF32;
-            if (valid) {
-                v = a.far_scan ? i : ldcg_u32(&fs[i]);
-                d = sssp_label<NARROW>(a, v) >> 32;
+        // SPLIT_ILP chunks of 32 per warp step, their loads issued together.
+        // A vertex is met once here (the pile holds it once, the scan visits
+        // each id once) and nothing relaxes during the split, so its near
+        // stamp is a plain store.
+        for (uint32_t b = warp * 32 * SPLIT_ILP; b < n_split; b += nwarps * 32 * SPLIT_ILP) {
+            uint32_t v[SPLIT_ILP], deg[SPLIT_ILP];
+            uint64_t d[SPLIT_ILP];
+            bool to_near[SPLIT_ILP], cand[SPLIT_ILP], keep[SPLIT_ILP];
+#pragma unroll
+            for (int c = 0; c < SPLIT_ILP; ++c) {
+                const uint32_t i = b + 32u * c + lane;
+                v[c] = 0;
+                d[c] = INF32;
+                if (i < n_split) v[c] = a.far_scan ? i : ldcg_u32(&fs[i]);
             }
-            valid = valid && d != INF32;                      // unreached
-            bool to_near = valid && d >= T_old && d < T;     // below T_old: already settled
-            bool keep = valid && d >= T;
-            if (to_near) {
-                uint32_t r0 = a.row_ptr[v], r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];
-                to_near = atomicExch(&a.stamp_near[v], u.tag_next) != u.tag_next;
-                deg = r1 - r0;
+#pragma unroll
+            for (int c = 0; c < SPLIT_ILP; ++c)
+                if (b + 32u * c + lane < n_split) d[c] = sssp_label<NARROW>(a, v[c]) >> 32;
+#pragma unroll
+            for (int c = 0; c < SPLIT_ILP; ++c) {
+                const bool valid = d[c] != INF32;                  // unreached or past the end
+                to_near[c] = valid && d[c] >= T_old && d[c] < T;   // below T_old: already settled
+                cand[c] = valid && d[c] >= T;
+                deg[c] = 0;
+                if (to_near[c]) {
+                    const uint32_t r0 = a.row_ptr[v[c]];
+                    const uint32_t r1 = a.lend ? a.lend[v[c]] : a.row_ptr[v[c] + 1];
+                    a.stamp_near[v[c]] = u.tag_next;
+                    deg[c] = r1 - r0;
+                }
+                keep[c] = cand[c] && !a.far_scan &&
+                          atomicExch(&a.stamp_far[v[c]], u.tag_far) != u.tag_far;
             }
-            const bool cand = keep;
-            if (keep) keep = !a.far_scan && atomicExch(&a.stamp_far[v], u.tag_far) != u.tag_far;
-            push_near(a, st, u, to_near, v, deg);
-            push_far(a, st, u, keep, cand, v, (uint32_t)d);
+#pragma unroll
+            for (int c = 0; c < SPLIT_ILP; ++c) {
+                push_near(a, st, u, to_near[c], v[c], deg[c]);
+                push_far(a, st, u, keep[c], cand[c], v[c], (uint32_t)d[c]);
+            }
         }
         flush_stage(st, u, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {

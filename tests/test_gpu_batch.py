@@ -37,14 +37,20 @@ def _check(g, seed_sets, results):
         assert r.total == ref.total, i
 
 
-def test_batch_64_queries_log_uniform_sizes():
+@pytest.mark.parametrize("tails", [0, 1])
+def test_batch_64_queries_log_uniform_sizes(tails):
+    """64 queries in one batch; the tails (MST, expansion, sorted edges) of
+    the queries that finish together run batched (1) or one at a time (0)."""
     g = wl.rmat(14, 16, wmax=1000, seed=41)
     pool = wl.largest_cc(g)
     sizes = wl.log_uniform_sizes(64, 3, 300, 7)
     qs = _queries(pool, sizes, 1)
     with st.SteinerGraph(g) as Gd:
+        Gd.set_param("batch_tails", tails)
         rc, res = Gd.query_batch(qs)
+        batches = Gd.get_param("batch_tail_batches")
     assert rc == st.STEINER_OK
+    assert (batches > 0) == bool(tails)
     _check(g, qs, res)
 
 
@@ -62,22 +68,31 @@ def test_batch_more_queries_than_slots_reuses_slots():
         assert np.array_equal(a.edges, b.edges) and a.total == b.total
 
 
-def test_batch_high_diameter_grid():
+@pytest.mark.parametrize("tails", [0, 1])
+def test_batch_high_diameter_grid(tails):
     g = wl.grid(300, 200, 1000, seed=43)
     pool = np.arange(g.n, dtype=np.int32)
     qs = _queries(pool, [2, 5, 17, 64, 3, 200, 9, 40], 3)
     with st.SteinerGraph(g) as Gd:
+        Gd.set_param("batch_tails", tails)
         rc, res = Gd.query_batch(qs)
     assert rc == st.STEINER_OK
     _check(g, qs, res)
 
 
-def test_batch_mixed_statuses_and_degenerate_queries():
-    e = np.array([[0, 1, 3], [1, 2, 4], [3, 4, 5], [4, 5, 1], [5, 6, 2], [0, 2, 9]])
-    g = wl.from_edges(9, e[:, 0], e[:, 1], e[:, 2])
+@pytest.mark.parametrize("tails", [0, 1])
+def test_batch_mixed_statuses_and_degenerate_queries(tails):
+    """Disconnected seed sets (forests), a single seed, duplicates, an
+    unreachable vertex and an overflowing distance in one batch."""
+    big = 0xFFFFFFFF // 2 + 1
+    e = np.array([[0, 1, 3], [1, 2, 4], [3, 4, 5], [4, 5, 1], [5, 6, 2], [0, 2, 9],
+                  [9, 10, big], [10, 11, big]])
+    g = wl.from_edges(12, e[:, 0], e[:, 1], e[:, 2])
     qs = [np.array([0, 2]), np.array([0, 5]), np.array([4]), np.array([3, 3]),
-          np.array([1, 2, 3, 6]), np.array([8, 0]), np.array([2, 0, 1])]
+          np.array([1, 2, 3, 6]), np.array([8, 0]), np.array([2, 0, 1]), np.array([9, 11]),
+          np.array([9, 10, 1, 4])]
     with st.SteinerGraph(g) as Gd:
+        Gd.set_param("batch_tails", tails)
         rc, res = Gd.query_batch(qs)
         alone = [Gd.query(s) for s in qs]
     assert rc != st.STEINER_OK
@@ -201,3 +216,25 @@ def test_batch_light_heavy_split(batch_delta):
             rc, res = Gd.query_batch(qs)
         assert rc == st.STEINER_OK
         _check(g, qs, res)
+
+
+def test_batched_tails_many_seeds_and_shared_vertices():
+    """Tails of queries with large seed sets (pair tables of many tiles, the
+    MST over thousands of pairs in one block) finishing together, on an
+    R-MAT graph whose hubs lie in many queries' trees (the walkers of
+    different queries cross the same vertices): batched and one-at-a-time
+    tails give the oracle's trees."""
+    g = wl.rmat(15, 16, wmax=100, seed=48)
+    pool = wl.largest_cc(g)
+    qs = _queries(pool, [2000, 3, 700, 2000, 64, 1500, 9, 2], 6)
+    out = {}
+    for tails in (1, 0):
+        with st.SteinerGraph(g) as Gd:
+            Gd.set_param("batch_tails", tails)
+            rc, out[tails] = Gd.query_batch(qs)
+            if tails:
+                assert Gd.get_param("batch_tail_batches") > 0
+        assert rc == st.STEINER_OK
+    _check(g, qs, out[1])
+    for a, b in zip(out[1], out[0]):
+        assert np.array_equal(a.edges, b.edges) and a.total == b.total
