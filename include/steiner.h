@@ -215,6 +215,10 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  converged (1..64, default 1: whole waves), or earlier
  *                  when a request waits and a slot is free
  *   "max_iters"    frontier iteration cap (STEINER_ETIMEOUT beyond it)
+ *   "dense"        1 (default): where splits scan the labels and no local
+ *                  rounds run, a large frontier is kept as a bitmap (one bit
+ *                  per vertex) that the next iteration reads in vertex
+ *                  order, and so is the list of a band's vertices; 0: queues
  *   "far_scan"     how a band split finds the vertices left for later
  *                  bands: -1 (default) chooses, 0 keeps a pile of them
  *                  (one stamp exchange and queue slot per improvement),

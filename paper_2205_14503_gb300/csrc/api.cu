@@ -78,6 +78,9 @@ struct steiner_graph {
     // Band splits: -1 chooses (a scan of the labels while the light/heavy
     // split is on, else the far pile), 0 / 1 force the pile / the scan.
     int far_scan = -1;
+    // Dense frontiers (bitmaps for large frontiers and band lists) wherever
+    // the far scan runs without local rounds; 0 turns them off.
+    uint32_t dense = 1;
     uint32_t narrow_fail_dbits = 0;   // most distance bits a narrow attempt ran out of
     uint32_t last_label_bits = 0;
     uint64_t narrow_reruns = 0;
@@ -103,6 +106,13 @@ int ensure_n_workspace(steiner_graph *G) {
     CK(dalloc(ws.band_q, n));
     CK(dalloc(ws.band_hq, G->g.heavy_chunk_cap));
     CK(dalloc(ws.mark, n));
+    const uint64_t words = ((uint64_t)n + 31) / 32;
+    CK(dalloc(ws.nbm[0], words));
+    CK(dalloc(ws.nbm[1], words));
+    CK(dalloc(ws.bbm, words));
+    CK(cudaMemsetAsync(ws.nbm[0], 0, words * 4, G->stream));
+    CK(cudaMemsetAsync(ws.nbm[1], 0, words * 4, G->stream));
+    CK(cudaMemsetAsync(ws.bbm, 0, words * 4, G->stream));
     CK(dalloc(ws.q[0], n));
     CK(dalloc(ws.q[1], n));
     CK(dalloc(ws.hq[0], G->g.heavy_chunk_cap));
@@ -197,6 +207,11 @@ void advance_epochs(Workspace &ws, const Control &c, cudaStream_t s) {
         cudaMemsetAsync(ws.stamp_far, 0, (size_t)ws.n * 4, s);
         cudaMemsetAsync(ws.stamp_band, 0, (size_t)ws.n * 4, s);
         cudaMemsetAsync(ws.mark, 0, (size_t)ws.n * 4, s);
+        // a run that stopped early may leave frontier bits set
+        const size_t words = ((size_t)ws.n + 31) / 32;
+        cudaMemsetAsync(ws.nbm[0], 0, words * 4, s);
+        cudaMemsetAsync(ws.nbm[1], 0, words * 4, s);
+        cudaMemsetAsync(ws.bbm, 0, words * 4, s);
         ws.epoch_near = ws.epoch_far = ws.epoch_mark = ws.epoch_band = 1;
     }
 }
@@ -226,8 +241,9 @@ int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool ful
     const bool split_on = G->delta <= G->g.max_w;
     const uint32_t far_scan = G->far_scan < 0 ? (split_on ? 1u : 0u) : (uint32_t)G->far_scan;
     static const bool trace = getenv("STEINER_TRACE") != nullptr;
+    const uint32_t dense = (G->dense && far_scan && G->local_rounds == 0) ? 1u : 0u;
     SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
-                 ws.epoch_band, far_scan, trace ? 1u : 0u};
+                 ws.epoch_band, far_scan, trace ? 1u : 0u, dense};
     CK(cudaEventRecord(G->ev[0], s));
     CK(ensure_partition(G, G->delta));
     CK(launch_init(G->g, ws, k, G->delta, s));
@@ -488,6 +504,14 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
         }
     }
     G->g.n_heavy_chunks = (uint32_t)chunks.size();
+    // ids at or above n_big have fewer than HEAVY_DEG arcs: with the degree
+    // order the hubs come first; without it no id is known to be light
+    G->g.n_big = n;
+    if (relabel) {
+        uint32_t nb = 0;
+        while (nb < n && irp[nb + 1] - irp[nb] >= HEAVY_DEG) ++nb;
+        G->g.n_big = nb;
+    }
     G->g.heavy_chunk_cap = (uint32_t)std::max<uint64_t>(cap, 1);
     if ((e = dalloc(G->g.row_ptr, (uint64_t)n + 1)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     if ((e = dalloc(G->g.adj, n_arcs)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
@@ -576,7 +600,7 @@ void steiner_free_graph(steiner_graph_t G) {
     cudaSetDevice(G->device);
     if (G->stream) cudaStreamSynchronize(G->stream);
     Workspace &ws = G->ws;
-    void *bufs[] = {ws.label, ws.label32, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.stamp_band, ws.band_q,
+    void *bufs[] = {ws.label, ws.label32, ws.nbm[0], ws.nbm[1], ws.bbm, ws.pred_arc, ws.stamp_near, ws.stamp_far, ws.stamp_band, ws.band_q,
                     ws.band_hq, ws.mark, ws.q[0], ws.q[1],
                     ws.hq[0], ws.hq[1], ws.far[0], ws.far[1], ws.ctl, ws.seeds, ws.pairtab,
                     ws.e_key, ws.e_ra, ws.e_rb, ws.e_arc, ws.e_mst, ws.tile_off, ws.comp, ws.hook,
@@ -608,6 +632,9 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     } else if (!strcmp(key, "local_rounds")) {
         if (value < 0 || value > 1024) return fail(STEINER_EINVAL, "local_rounds out of range");
         G->local_rounds = (uint32_t)value;
+    } else if (!strcmp(key, "dense")) {
+        if (value != 0 && value != 1) return fail(STEINER_EINVAL, "dense must be 0 or 1");
+        G->dense = (uint32_t)value;
     } else if (!strcmp(key, "far_scan")) {
         if (value < -1 || value > 1) return fail(STEINER_EINVAL, "far_scan must be -1, 0 or 1");
         G->far_scan = (int)value;
@@ -635,6 +662,7 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "heavy_chunks")) return G->g.n_heavy_chunks;
     if (!strcmp(key, "label_bits")) return G->label_bits;
     if (!strcmp(key, "far_scan")) return G->far_scan;
+    if (!strcmp(key, "dense")) return G->dense;
     if (!strcmp(key, "label_bits_last")) return G->last_label_bits;
     if (!strcmp(key, "narrow_reruns")) return (int64_t)G->narrow_reruns;
     if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);

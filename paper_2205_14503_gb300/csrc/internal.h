@@ -39,6 +39,9 @@ struct DevGraph {
     uint2 *adj_w = nullptr;
     uint32_t *lend = nullptr;
     uint32_t part_delta = 0;        // 0: not built
+    // Vertices with ids at or above n_big have fewer than HEAVY_DEG arcs
+    // (the descending-degree order puts the hubs first; n without it).
+    uint32_t n_big = 0;
 };
 
 // The weight-partitioned rows to use for band width delta: built for that
@@ -116,6 +119,10 @@ struct Workspace {
     uint32_t *band_q = nullptr;      // vertices relaxed in the current band, n
     uint64_t *band_hq = nullptr;     // their heavy-row chunks, heavy_chunk_cap
     uint32_t *mark = nullptr;       // tree-walk stamps
+    // dense frontiers: near bitmaps (alternating by iteration) and the band
+    // bitmap, ceil(n / 32) words each, all zero between queries
+    uint32_t *nbm[2] = {nullptr, nullptr};
+    uint32_t *bbm = nullptr;
     uint32_t *q[2] = {nullptr, nullptr};      // light frontier
     uint64_t *hq[2] = {nullptr, nullptr};     // heavy-chunk frontier
     uint32_t *far[2] = {nullptr, nullptr};
@@ -161,6 +168,7 @@ struct SsspParams {
     uint32_t base_band;      // first band-list tag of this query
     uint32_t far_scan;       // splits scan the labels instead of a far pile
     uint32_t trace;          // per-iteration relaxation counts into Control::trace_relax
+    uint32_t dense;          // dense frontiers (needs far_scan and no local rounds)
 };
 
 // SM count of the current device (queried once per device, then cached);

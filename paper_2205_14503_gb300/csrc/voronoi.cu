@@ -56,6 +56,17 @@ struct SsspArgs {
     uint32_t defer;          // light/heavy arc split on
     uint32_t far_scan;       // no far pile: splits find far vertices by scanning the labels
     uint32_t trace;          // record per-iteration relaxation counts
+    // Dense frontiers (with the far scan, without local rounds): a large
+    // frontier is a bitmap (one bit per vertex, set with a fire-and-forget
+    // atomicOr) read in id order by the next iteration, and the band list
+    // of the light/heavy split is a bitmap too; hubs keep their chunk
+    // queues.  Ids below n_big may have HEAVY_DEG arcs or more, ids at or
+    // above it have fewer (the degree order makes this a bound).
+    uint32_t dense;
+    uint32_t n_big;
+    uint32_t n_words;        // bitmap words, ceil(n / 32)
+    uint32_t *nbm0, *nbm1;   // near bitmaps, alternating by iteration
+    uint32_t *bbm;           // band bitmap
     // with the split: end of each row's light part in the weight-partitioned
     // adjacency `adj` (null: rows are unpartitioned and arcs are filtered)
     const uint32_t *lend;
@@ -120,6 +131,8 @@ constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
 constexpr uint32_t BAND_STAGE = 2048;  // block staging capacity (band-list items)
 constexpr uint32_t BAND_REGION = BAND_STAGE / SSSP_WARPS;
 constexpr int SPLIT_ILP = 4;           // 32-vertex chunks per warp step in a band split
+constexpr uint32_t DENSE_WORDS = 32;   // bitmap words per dense work item (light arcs)
+constexpr uint32_t DENSE_WORDS_HP = 32;   // the same in a heavy-arc pass
 
 // Where the appends of one processing segment go.
 struct PushTargets {
@@ -138,6 +151,10 @@ struct PushTargets {
     // A full warp region may move to the global queue mid-segment (not
     // during the warp-local rounds, which index into the region).
     bool flush;
+    // Near pushes of light vertices set bits of nbm (the next iteration
+    // reads the bitmap) instead of going through the queue.
+    bool dense;
+    uint32_t *nbm;
 };
 
 // Per-block staging buffers.  Near and band-list appends go to one region
@@ -152,6 +169,8 @@ struct Stage {
     uint32_t far_buf[FAR_STAGE];
     uint32_t band_buf[BAND_STAGE];
     uint32_t band_n[SSSP_WARPS];    // items staged per band region
+    uint32_t dn_near[SSSP_WARPS];   // bits set in the near bitmap by each warp
+    uint32_t dn_band[SSSP_WARPS];   // bits set in the band bitmap by each warp
     uint32_t near_n[SSSP_WARPS];    // items staged per warp region
     uint32_t local_lo[SSSP_WARPS];  // region[0, local_lo) was relaxed by its warp already
     uint32_t near_off[SSSP_WARPS];  // flush: offset of each region's rest
@@ -167,6 +186,8 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
     if (threadIdx.x < SSSP_WARPS) {
         st.near_n[threadIdx.x] = 0;
         st.band_n[threadIdx.x] = 0;
+        st.dn_near[threadIdx.x] = 0;
+        st.dn_band[threadIdx.x] = 0;
         st.local_lo[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -189,6 +210,16 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
         st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
         st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
         if (st.far_min != INF32) atomicMin(t.far_min, st.far_min);
+        // bits set in the bitmaps count as items (a vertex set twice counts
+        // twice): the counts only size the next iteration and show that a
+        // frontier or band list is non-empty
+        uint32_t dnn = 0, dnb = 0;
+        for (uint32_t w = 0; w < SSSP_WARPS; ++w) {
+            dnn += st.dn_near[w];
+            dnb += st.dn_band[w];
+        }
+        if (dnn) atomicAdd(t.qn_count, dnn);
+        if (dnb) atomicAdd(t.band_count, dnb);
     }
     __syncthreads();
     {   // each warp moves the rest of its own regions
@@ -318,16 +349,29 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
     }
     // rounds that improve nothing skip the append machinery
     if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
-    bool to_near[ILP], to_far[ILP], cand[ILP];
+    bool to_near[ILP], to_far[ILP], cand[ILP], dn[ILP];
     uint32_t deg[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-        to_near[u] = to_far[u] = cand[u] = false;
+        to_near[u] = to_far[u] = cand[u] = dn[u] = false;
         deg[u] = 0;
         if (!imp[u]) continue;
         ++improved;
         uint32_t v = e[u].x;
-        if (nd[u] < t.T) {
+        if (nd[u] < t.T && t.dense) {
+            // a light vertex sets its bit; a possible hub (id below n_big)
+            // reads its degree first and, if it is one, joins the chunk queue
+            if (v < a.n_big) {
+                const uint32_t r0 = a.row_ptr[v];
+                deg[u] = (a.lend ? a.lend[v] : a.row_ptr[v + 1]) - r0;
+            }
+            if (deg[u] >= HEAVY_DEG) {
+                to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
+            } else {
+                atomicOr(&t.nbm[v >> 5], 1u << (v & 31));
+                dn[u] = true;
+            }
+        } else if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v];                           // independent of the exchange
             uint32_t r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
             // with local rounds a staged vertex may be relaxed this very
@@ -347,6 +391,12 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         push_near(a, st, t, to_near[u], e[u].x, deg[u]);
         push_far(a, st, t, to_far[u], cand[u], e[u].x, (uint32_t)nd[u]);
     }
+    if (t.dense) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) c += (uint32_t)__popc(__ballot_sync(FULL, dn[u]));
+        if (lane_id() == 0 && c) st.dn_near[threadIdx.x >> 5] += c;
+    }
 }
 
 // Lists vertex u (lanes with `want`; hdeg arcs in its heavy part) in the
@@ -354,6 +404,15 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
 // part is long.  A vertex without heavy arcs needs no listing.
 __device__ __forceinline__ void band_track(const SsspArgs &a, Stage &st, bool want, uint32_t u,
                                            uint32_t hdeg, uint32_t tag) {
+    if (a.dense) {
+        // dense band list: a bit per listed vertex (the pass reads the
+        // bitmap), so only the hubs need the stamp that lists them once
+        const bool small = want && hdeg > 0 && hdeg < HEAVY_DEG;
+        if (small) atomicOr(&a.bbm[u >> 5], 1u << (u & 31));
+        const uint32_t c = (uint32_t)__popc(__ballot_sync(FULL, small));
+        if (lane_id() == 0 && c) st.dn_band[threadIdx.x >> 5] += c;
+        want = want && hdeg >= HEAVY_DEG;
+    }
     bool add = want && hdeg > 0 && atomicExch(&a.stamp_band[u], tag) != tag;
     const bool big = add && hdeg >= HEAVY_DEG;
     const uint32_t w = threadIdx.x >> 5;
@@ -390,6 +449,71 @@ __device__ __forceinline__ void band_track_heavy(const SsspArgs &a, uint32_t u, 
     for (uint32_t c = lane; c < nc; c += 32) a.band_hq[base + c] = ((uint64_t)u << 32) | c;
 }
 
+// Relaxes the arcs of up to 32 frontier vertices, one per lane (has, u),
+// flattened over the lanes: their light parts (their heavy parts in a
+// band's closing pass, hp), listing them for the band when tracked.
+template <bool NARROW>
+__device__ __forceinline__ void relax_vertices(const SsspArgs &a, Stage &st, const PushTargets &t,
+                                               bool has, uint32_t u, bool hp, bool track,
+                                               uint32_t tag_band, uint32_t wlo, uint32_t whi,
+                                               bool precheck, unsigned long long &attempts,
+                                               unsigned long long &improved, bool &narrow_miss,
+                                               unsigned long long &atomics) {
+    const uint32_t lane = lane_id();
+    uint32_t s = 0, deg = 0, hdeg = 0;
+    uint64_t lab = INF64;
+    if (has) {
+        const uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
+        const uint32_t le = a.lend ? a.lend[u] : r1;
+        if (hp) {                       // the heavy part (or the whole row)
+            s = a.lend ? le : r0;
+            deg = r1 - s;
+        } else {                        // the light part
+            s = r0;
+            deg = le - r0;
+            hdeg = a.lend ? r1 - le : r1 - r0;
+        }
+        lab = sssp_label<NARROW>(a, u);
+        if (lab == INF64) deg = 0;
+    }
+    if (track) band_track(a, st, has, u, hdeg, tag_band);
+    const uint32_t incl = warp_inclusive_scan(deg);
+    const uint32_t excl = incl - deg;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t b = 0; b < total; b += 32 * ILP) {
+        bool valid[ILP];
+        uint32_t arc[ILP];
+        uint64_t labs[ILP];
+#pragma unroll
+        for (int q = 0; q < ILP; ++q) {
+            const uint32_t j = b + lane + 32 * q;
+            valid[q] = j < total;
+            const uint32_t owner = warp_owner_search(excl, valid[q] ? j : 0);
+            const uint32_t so = __shfl_sync(FULL, s, owner);
+            const uint32_t eo = __shfl_sync(FULL, excl, owner);
+            labs[q] = __shfl_sync(FULL, lab, owner);
+            arc[q] = so + (j - eo);
+        }
+        relax_group<NARROW>(a, st, t, valid, arc, labs, precheck, false, wlo, whi, attempts,
+                            improved, narrow_miss, atomics);
+    }
+}
+
+// Index of the t-th set bit (0-based) of a 32-bit word.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t t) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t w = 16; w >= 1; w >>= 1) {
+        const uint32_t c = (uint32_t)__popc(x & ((1u << w) - 1u));
+        if (t >= c) {
+            t -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // ---------------------------------------------------------------------------
 // the persistent near/far kernel
 // ---------------------------------------------------------------------------
@@ -409,6 +533,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     uint64_t T = a.delta;
     bool first = (blockIdx.x == 0 && threadIdx.x == 0);
     bool hp = false;               // this iteration is a band's heavy-arc pass
+    bool cur_dense = false;        // this iteration's light items are the bits of a near bitmap
 
     for (;;) {
         const uint32_t cs = it % 3, ns = (it + 1) % 3;
@@ -450,6 +575,17 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         t.tag_far = a.base_far + phase;
         t.T = T;
         t.flush = true;
+        // dense in: light items from this iteration's near bitmap (or, in a
+        // dense heavy-arc pass, the band bitmap); dense out: a large
+        // frontier (a fraction of the graph, or many hub chunks) pushes its
+        // light vertices as bits for the next iteration.  Every block reads
+        // the same counts, so all agree.
+        const bool dense_in = hp ? a.dense != 0 : cur_dense;
+        const bool push_dense =
+            a.dense && !hp && (n_light >= a.n / 128 || n_heavy >= a.n / 4096);
+        uint32_t *bm_in = hp ? a.bbm : ((it & 1) ? a.nbm1 : a.nbm0);
+        t.dense = push_dense;
+        t.nbm = (it & 1) ? a.nbm0 : a.nbm1;
         // arcs relaxed by this iteration: all; light ones while a band
         // iterates under the split; heavy ones in the band's closing pass
         const uint32_t wlo = hp ? a.delta : 0u;
@@ -461,7 +597,14 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         // (fewer sequential rounds per warp), a thick one packs 32 per warp.
         uint32_t per = (n_light + nwarps - 1) / nwarps;
         uint32_t bsz = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : per <= 8 ? 8 : per <= 16 ? 16 : 32;
-        const uint32_t n_work = n_heavy + (n_light + bsz - 1) / bsz;
+        // A dense work item is one bitmap word (32 vertices) where vertices
+        // may have many arcs (ids below n_big, in the degree order the high
+        // degrees), else DENSE_WORDS words: balanced work per warp.  In a
+        // heavy-arc pass every vertex relaxes its heavier arcs: one word.
+        const uint32_t cw = hp ? DENSE_WORDS_HP : DENSE_WORDS;
+        const uint32_t fine = min(a.n_words, (a.n_big + 1023) / 1024 * 32);
+        const uint32_t n_work = n_heavy + (dense_in ? fine + (a.n_words - fine + cw - 1) / cw
+                                                    : (n_light + bsz - 1) / bsz);
         if (a.trace) t_start = global_ns();
         for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
             if (wi < n_heavy) {
@@ -489,48 +632,38 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                     relax_group<NARROW>(a, st, t, valid, arc, labs, true, true, wlo, whi, attempts,
                                 improved, narrow_miss, atomics);
                 }
+            } else if (dense_in) {
+                // 1 or 32 words of the bitmap, one per lane (read and
+                // cleared); their set bits, 32 at a time, are the vertices
+                const uint32_t di = wi - n_heavy;
+                const uint32_t w0 = di < fine ? di : fine + (di - fine) * cw;
+                const uint32_t nw = di < fine ? 1u : cw;
+                uint32_t word = 0;
+                if (lane < nw && w0 + lane < a.n_words) {
+                    word = ldcg_u32(&bm_in[w0 + lane]);
+                    if (word) bm_in[w0 + lane] = 0;
+                }
+                const uint32_t cnt = (uint32_t)__popc(word);
+                const uint32_t incl = warp_inclusive_scan(cnt);
+                const uint32_t excl = incl - cnt;
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                for (uint32_t b = 0; b < total; b += 32) {
+                    const uint32_t j = b + lane;
+                    const bool has = j < total;
+                    const uint32_t owner = warp_owner_search(excl, has ? j : 0);
+                    const uint32_t wo = __shfl_sync(FULL, word, owner);
+                    const uint32_t eo = __shfl_sync(FULL, excl, owner);
+                    const uint32_t u = has ? (w0 + owner) * 32 + nth_set_bit(wo, j - eo) : 0;
+                    relax_vertices<NARROW>(a, st, t, has, u, hp, track, tag_band, wlo, whi, true,
+                                           attempts, improved, narrow_miss, atomics);
+                }
             } else {
                 // bsz frontier vertices per warp, their arcs flattened over the lanes
-                uint32_t i = (wi - n_heavy) * bsz + lane;
-                bool has = lane < bsz && i < n_light;
-                uint32_t s = 0, deg = 0, u = 0, hdeg = 0;
-                uint64_t lab = INF64;
-                if (has) {
-                    u = ldcg_u32(&qc[i]);
-                    const uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
-                    const uint32_t le = a.lend ? a.lend[u] : r1;
-                    if (hp) {                       // the heavy part (or the whole row)
-                        s = a.lend ? le : r0;
-                        deg = r1 - s;
-                    } else {                        // the light part
-                        s = r0;
-                        deg = le - r0;
-                        hdeg = a.lend ? r1 - le : r1 - r0;
-                    }
-                    lab = sssp_label<NARROW>(a, u);
-                    if (lab == INF64) deg = 0;
-                }
-                if (track) band_track(a, st, has, u, hdeg, tag_band);
-                uint32_t incl = warp_inclusive_scan(deg);
-                uint32_t excl = incl - deg;
-                uint32_t total = __shfl_sync(FULL, incl, 31);
-                for (uint32_t b = 0; b < total; b += 32 * ILP) {
-                    bool valid[ILP];
-                    uint32_t arc[ILP];
-                    uint64_t labs[ILP];
-#pragma unroll
-                    for (int q = 0; q < ILP; ++q) {
-                        uint32_t j = b + lane + 32 * q;
-                        valid[q] = j < total;
-                        uint32_t owner = warp_owner_search(excl, valid[q] ? j : 0);
-                        uint32_t so = __shfl_sync(FULL, s, owner);
-                        uint32_t eo = __shfl_sync(FULL, excl, owner);
-                        labs[q] = __shfl_sync(FULL, lab, owner);
-                        arc[q] = so + (j - eo);
-                    }
-                    relax_group<NARROW>(a, st, t, valid, arc, labs, bsz == 32, false, wlo, whi,
-                                attempts, improved, narrow_miss, atomics);
-                }
+                const uint32_t i = (wi - n_heavy) * bsz + lane;
+                const bool has = lane < bsz && i < n_light;
+                const uint32_t u = has ? ldcg_u32(&qc[i]) : 0;
+                relax_vertices<NARROW>(a, st, t, has, u, hp, track, tag_band, wlo, whi, bsz == 32,
+                                       attempts, improved, narrow_miss, atomics);
             }
         }
         // Local rounds: relax the vertices just staged for the next
@@ -621,6 +754,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             if (first) ctl->exit_reason = 3;
             break;
         }
+        cur_dense = push_dense;
         ++it;
         const bool was_hp = hp;
         if (hp) {
@@ -688,6 +822,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.tag_far = a.base_far + phase;
         u.T = T;
         u.flush = true;
+        u.dense = a.dense;
+        u.nbm = (its & 1) ? a.nbm1 : a.nbm0;
         // the far pile, or with the far scan every vertex (coalesced labels)
         const uint32_t n_split = a.far_scan ? a.n : nf;
         // SPLIT_ILP chunks of 32 per warp step, their loads issued together.
@@ -714,7 +850,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 to_near[c] = valid && d[c] >= T_old && d[c] < T;   // below T_old: already settled
                 cand[c] = valid && d[c] >= T;
                 deg[c] = 0;
-                if (to_near[c]) {
+                // dense: ids at or above n_big are light without a look at the row
+                if (to_near[c] && (!a.dense || v[c] < a.n_big)) {
                     const uint32_t r0 = a.row_ptr[v[c]];
                     const uint32_t r1 = a.lend ? a.lend[v[c]] : a.row_ptr[v[c] + 1];
                     a.stamp_near[v[c]] = u.tag_next;
@@ -725,7 +862,15 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             }
 #pragma unroll
             for (int c = 0; c < SPLIT_ILP; ++c) {
-                push_near(a, st, u, to_near[c], v[c], deg[c]);
+                // dense (with the far scan a chunk is one bitmap word, empty
+                // since the band drained): light vertices as one word store
+                const bool bit = u.dense && to_near[c] && deg[c] < HEAVY_DEG;
+                const uint32_t word = __ballot_sync(FULL, bit);
+                if (lane == 0 && word) {
+                    u.nbm[(b + 32u * c) >> 5] = word;
+                    st.dn_near[threadIdx.x >> 5] += (uint32_t)__popc(word);
+                }
+                push_near(a, st, u, to_near[c] && !bit, v[c], deg[c]);
                 push_far(a, st, u, keep[c], cand[c], v[c], (uint32_t)d[c]);
             }
         }
@@ -739,6 +884,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             ctl->far_min[fc] = INF32;
         }
         it = its;
+        cur_dense = a.dense;          // the split set the next frontier's bits
         if (it >= a.max_iters) {
             if (first) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
@@ -864,6 +1010,12 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.defer = p.delta <= g.max_w ? 1u : 0u;
     a.far_scan = p.far_scan;
     a.trace = p.trace;
+    a.dense = p.dense;
+    a.n_big = g.n_big;
+    a.n_words = (g.n + 31) / 32;
+    a.nbm0 = ws.nbm[0];
+    a.nbm1 = ws.nbm[1];
+    a.bbm = ws.bbm;
     a.lend = active_lend(g, p.delta);
     if (a.lend) a.adj = g.adj_w;        // rows partitioned by weight class
     void *args[] = {&a};

@@ -408,3 +408,19 @@ def test_seed_selection_strategies(strategy):
                 "proximate": wl.seeds_proximate}[strategy]
         seeds = make(g, pool, 40, 73)
         _compare_forced(g, seeds)
+
+
+@pytest.mark.parametrize("dense", [0, 1])
+@pytest.mark.parametrize("relabel", ["0", "1"])
+def test_dense_frontiers(dense, relabel, monkeypatch):
+    """Large frontiers and the band lists of the light/heavy split kept as
+    bitmaps read in vertex order (dense) or as queues; with the internal
+    degree order (hubs first, so an id tells a light vertex) and without;
+    band widths below, near and above the weights.  Every output equals
+    the oracle's."""
+    monkeypatch.setenv("STEINER_RELABEL", relabel)
+    for g, k in ((wl.rmat(14, 16, wmax=1000, seed=81), 400),
+                 (wl.rmat(13, 48, wmax=100, seed=82), 60)):
+        seeds = wl.sample_distinct(wl.largest_cc(g), k, 83)
+        for delta in (30, 200, 5000):
+            _compare_forced(g, seeds, dense=dense, far_scan=1, delta=delta, local_rounds=0)
