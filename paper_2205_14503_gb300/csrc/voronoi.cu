@@ -131,8 +131,8 @@ constexpr uint32_t FAR_STAGE = 1024;   // block staging capacity (far items)
 constexpr uint32_t BAND_STAGE = 2048;  // block staging capacity (band-list items)
 constexpr uint32_t BAND_REGION = BAND_STAGE / SSSP_WARPS;
 constexpr int SPLIT_ILP = 4;           // 32-vertex chunks per warp step in a band split
-constexpr uint32_t DENSE_WORDS = 32;   // bitmap words per dense work item (light arcs)
-constexpr uint32_t DENSE_WORDS_HP = 32;   // the same in a heavy-arc pass
+constexpr uint32_t DENSE_WORDS = 8;    // bitmap words per dense work item (light arcs)
+constexpr uint32_t DENSE_WORDS_HP = 8; // the same in a heavy-arc pass
 
 // Where the appends of one processing segment go.
 struct PushTargets {
