@@ -167,13 +167,21 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def workload(rank: int, side: int | None = None, k: int | None = None, cfg: int = WORKLOAD):
+def workload(rank: int, side: int | None = None, k: int | None = None, cfg: int = WORKLOAD,
+             scale: int | None = None):
     """The benchmark graph, the timed seed set and the autotuner's held-out
     seed set (same size, same pool, another salt).  ``side``/``k`` shrink
-    the grid for profiling captures (same seed density); ``cfg`` picks the
+    the grid, ``scale``/``k`` the R-MAT graph, for profiling captures (same
+    recipe and seed density unless k is given); ``cfg`` picks the
     single-query workload (3 R-MAT 26, the default; 2 the grid; 1 R-MAT 16)."""
     import paper_2205_14503_gb300.workloads as wl
-    if side:
+    if scale:
+        c = wl.CONFIGS[3]
+        g = wl.rmat(scale, 16, (0.57, 0.19, 0.19), c["wmax"], wl.CONFIG_SEED + 3, True)
+        pool = wl.largest_cc(g)
+        kk = k or max(2, round(c["k"] * 2.0 ** (scale - c["scale"])))
+        seeds = wl.sample_distinct(pool, kk, (wl.CONFIG_SEED + 3) ^ 0x51ED)
+    elif side:
         g = wl.grid(side, side, 1000, wl.CONFIG_SEED + GRID)
         pool = np.arange(g.n, dtype=np.int32)
         seeds = wl.sample_distinct(pool, k or 64, (wl.CONFIG_SEED + GRID) ^ 0x51ED)
@@ -253,9 +261,13 @@ def finish_oracle_child(child):
         return {"error": "oracle child gave no result"}
 
 
-def config_dict(g, seeds, cfg: int = WORKLOAD, side: int | None = None):
+def config_dict(g, seeds, cfg: int = WORKLOAD, side: int | None = None,
+                scale: int | None = None):
     import paper_2205_14503_gb300.workloads as wl
-    if side or cfg == GRID:
+    if scale:
+        name = f"rmat{scale}_k{seeds.size}"
+        desc = f"R-MAT scale {scale}, edge factor 16, (a,b,c)=(.57,.19,.19), w~U[1,1000]"
+    elif side or cfg == GRID:
         s = int(round(g.n ** 0.5))
         name, desc = f"grid{s}_k{seeds.size}", f"{s}x{s} 4-connected grid, w~U[1,1000]"
     else:
@@ -282,7 +294,7 @@ def run_reference(args, world, rank):
     warm up, so no warm-up query runs when the budget is that short."""
     if rank != 0:
         return
-    g, seeds, _ = workload(0, args.side, args.k, args.workload)
+    g, seeds, _ = workload(0, args.side, args.k, args.workload, args.scale)
     import oracle
 
     def one():
@@ -314,7 +326,7 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": len(times), "warmup": warm,
             "ms_per_step": 1e3 * per_q, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_dict(g, seeds, args.workload, args.side),
+            "config": config_dict(g, seeds, args.workload, args.side, args.scale),
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "trees/s", "cores": 1,
                              "sample": f"{len(times)} whole queries of the workload, "
                                        "single-threaded C oracle", **host_info()},
@@ -336,7 +348,7 @@ def run_ours(args, world, rank, local):
     __graft_entry__.build()
     from paper_2205_14503_gb300 import steiner as st
 
-    g, seeds, tune_seeds = workload(rank, args.side, args.k, args.workload)
+    g, seeds, tune_seeds = workload(rank, args.side, args.k, args.workload, args.scale)
     # the CPU baseline runs beside the GPU measurement, in a child forked
     # before this process makes its first CUDA call
     child = (start_oracle_child(g, seeds)
@@ -416,7 +428,7 @@ def run_ours(args, world, rank, local):
     alg_bytes = (8 + lb) * m_arcs + (4 + lb) * n
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (sssp_ms / 1e3) / 1e9
-    cfgd = config_dict(g, seeds, args.workload, args.side)
+    cfgd = config_dict(g, seeds, args.workload, args.side, args.scale)
     traffic = profiled_traffic(cfgd["workload"])
     line = {
         "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world,
@@ -777,7 +789,11 @@ def main():
                          "(BLOCKS 0 = all; LABEL_BITS 0/32/64; FAR_SCAN -1/0/1)")
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
-    ap.add_argument("--k", type=int, default=None, help="profiling only: seeds for --side")
+    ap.add_argument("--k", type=int, default=None,
+                    help="profiling only: seeds for --side / --scale")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="profiling only: an R-MAT graph of this scale with the R-MAT 26 "
+                         "workload's recipe and seed density")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3],
                     help="plain mode: single-query workload (3 = R-MAT 26 with 10,000 seeds, "
                          "the default; 2 = the 4096^2 grid; 1 = R-MAT 16)")

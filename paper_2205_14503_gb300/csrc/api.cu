@@ -506,8 +506,8 @@ int steiner_load_graph(const uint32_t *row_ptr, const int32_t *col, const uint32
     G->g.n_heavy_chunks = (uint32_t)chunks.size();
     // ids at or above n_big have fewer than HEAVY_DEG arcs: with the degree
     // order the hubs come first; without it no id is known to be light
-    G->g.n_big = n;
-    if (relabel) {
+    G->g.n_big = max_deg < HEAVY_DEG ? 0 : n;
+    if (relabel && max_deg >= HEAVY_DEG) {
         uint32_t nb = 0;
         while (nb < n && irp[nb + 1] - irp[nb] >= HEAVY_DEG) ++nb;
         G->g.n_big = nb;

@@ -109,24 +109,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Exchanges with release / acquire semantics at GPU scope.  A relaxation
-// that improves a label then release-exchanges the vertex's queue stamp; a
-// block taking the vertex from its staging buffer acquire-exchanges the
-// same stamp before reading the label.  Both are read-modify-writes of one
-// location, so either the taker's exchange reads a releaser's stamp (and
-// then sees that label), or the releaser's exchange reads the taker's
-// stamp (and queues the vertex again): no improvement is lost.
-__device__ __forceinline__ uint32_t exch_release(uint32_t *p, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ uint32_t exch_acquire(uint32_t *p, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.acquire.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -193,16 +175,32 @@ __device__ __forceinline__ void stage_append(bool want, uint32_t v, uint32_t *bu
     if (g != INF32) gq[g] = v;
 }
 
+// Warp-aggregated append of v (lanes with `want`) to a global queue; with
+// a stamp array, only lanes whose exchange of stamp[v] to `tag` finds
+// another value append (the vertex joins the queue once per tag).  All
+// lanes call.
+__device__ __forceinline__ void queue_append(bool want, uint32_t v, uint32_t *gq, uint32_t *gcount,
+                                             uint32_t gcap, uint32_t *err, uint32_t *stamp,
+                                             uint32_t tag) {
+    if (want && stamp) want = atomicExch(&stamp[v], tag) != tag;
+    const uint32_t g = warp_append(want, gcount, gcap, err);
+    if (g != INF32) gq[g] = v;
+}
+
 // Warp-synchronous append of v (lanes with `want`) to this warp's own
 // region (region[0, *cnt), capacity cap; *cnt is written by this warp
 // only).  If the appends do not fit and `flush` allows it, the warp first
-// moves the region to the global queue (gq, *gcount, capacity gcap) with
-// one atomicAdd and starts the region over; otherwise the lanes that do
-// not fit go to the global queue directly.  All lanes call.
+// moves the region to the global queue (gq, *gcount, capacity gcap) and
+// starts the region over; otherwise the lanes that do not fit go to the
+// global queue directly.  Without a stamp array the move is one atomicAdd
+// for the whole region; with one (a region that may hold a vertex more than
+// once) every item is deduplicated against stamp[v] == tag on its way to
+// the queue.  All lanes call.
 __device__ __forceinline__ void region_append(bool want, uint32_t v, uint32_t *region,
                                               uint32_t *cnt, uint32_t cap, bool flush,
                                               uint32_t *gq, uint32_t *gcount, uint32_t gcap,
-                                              uint32_t *err) {
+                                              uint32_t *err, uint32_t *stamp = nullptr,
+                                              uint32_t tag = 0) {
     const uint32_t mask = __ballot_sync(FULL, want);
     if (mask == 0) return;
     const uint32_t lane = lane_id();
@@ -210,13 +208,19 @@ __device__ __forceinline__ void region_append(bool want, uint32_t v, uint32_t *r
     const uint32_t k = (uint32_t)__popc(mask);
     if (flush && n + k > cap) {
         n = min(n, cap);
-        uint32_t base = 0;
-        if (lane == 0 && n) base = atomicAdd(gcount, n);
-        base = __shfl_sync(FULL, base, 0);
-        for (uint32_t i = lane; i < n; i += 32) {
-            const uint32_t slot = base + i;
-            if (slot < gcap) gq[slot] = region[i];
-            else atomicOr(err, ERR_CAPACITY);
+        if (stamp) {
+            for (uint32_t i0 = 0; i0 < n; i0 += 32)
+                queue_append(i0 + lane < n, i0 + lane < n ? region[i0 + lane] : 0u, gq, gcount,
+                             gcap, err, stamp, tag);
+        } else {
+            uint32_t base = 0;
+            if (lane == 0 && n) base = atomicAdd(gcount, n);
+            base = __shfl_sync(FULL, base, 0);
+            for (uint32_t i = lane; i < n; i += 32) {
+                const uint32_t slot = base + i;
+                if (slot < gcap) gq[slot] = region[i];
+                else atomicOr(err, ERR_CAPACITY);
+            }
         }
         __syncwarp();       // the region is read out before it is refilled
         n = 0;
@@ -224,8 +228,7 @@ __device__ __forceinline__ void region_append(bool want, uint32_t v, uint32_t *r
     const uint32_t slot = n + (uint32_t)__popc(mask & lanemask_lt());
     const bool local = want && slot < cap;
     if (local) region[slot] = v;
-    const uint32_t g = warp_append(want && !local, gcount, gcap, err);
-    if (g != INF32) gq[g] = v;
+    queue_append(want && !local, v, gq, gcount, gcap, err, stamp, tag);
     __syncwarp();
     if (lane == 0) *(volatile uint32_t *)cnt = n + k;
     __syncwarp();

@@ -155,6 +155,12 @@ struct PushTargets {
     // reads the bitmap) instead of going through the queue.
     bool dense;
     uint32_t *nbm;
+    // With warp-local rounds: every improvement appends its vertex to the
+    // improving warp's region with no stamp (a region may hold a vertex
+    // twice, and a warp-local round simply reads the current label); the
+    // near stamps deduplicate items only on their way to the global queue.
+    bool nostamp;
+    uint32_t *nostamp_stamp;     // the near stamps (for the deduplication)
 };
 
 // Per-block staging buffers.  Near and band-list appends go to one region
@@ -205,7 +211,7 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
         for (uint32_t w = 0; w < SSSP_WARPS; ++w) {
             const uint32_t hi = min(st.near_n[w], NEAR_REGION), lo = st.local_lo[w];
             st.near_off[w] = nn;
-            nn += hi > lo ? hi - lo : 0;
+            if (!t.nostamp) nn += hi > lo ? hi - lo : 0;
         }
         st.base_near = nn ? atomicAdd(t.qn_count, nn) : 0;
         st.base_far = nf ? atomicAdd(t.far_count, nf) : 0;
@@ -225,10 +231,18 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
     {   // each warp moves the rest of its own regions
         const uint32_t w = threadIdx.x >> 5;
         const uint32_t hi = min(st.near_n[w], NEAR_REGION), lo = st.local_lo[w];
-        for (uint32_t i = lo + lane_id(); i < hi; i += 32) {
-            uint32_t slot = st.base_near + st.near_off[w] + (i - lo);
-            if (slot < n) t.qn[slot] = st.near_buf[w * NEAR_REGION + i];
-            else atomicOr(err, ERR_CAPACITY);
+        if (t.nostamp) {            // deduplicated on the way
+            for (uint32_t i0 = lo; i0 < hi; i0 += 32) {
+                const uint32_t i = i0 + lane_id();
+                queue_append(i < hi, i < hi ? st.near_buf[w * NEAR_REGION + i] : 0u, t.qn,
+                             t.qn_count, n, err, t.nostamp_stamp, t.tag_next);
+            }
+        } else {
+            for (uint32_t i = lo + lane_id(); i < hi; i += 32) {
+                uint32_t slot = st.base_near + st.near_off[w] + (i - lo);
+                if (slot < n) t.qn[slot] = st.near_buf[w * NEAR_REGION + i];
+                else atomicOr(err, ERR_CAPACITY);
+            }
         }
         const uint32_t nb = min(st.band_n[w], BAND_REGION);
         if (nb) {
@@ -255,7 +269,8 @@ __device__ __forceinline__ void push_near(const SsspArgs &a, Stage &st, const Pu
     bool heavy = want && deg >= HEAVY_DEG;
     const uint32_t w = threadIdx.x >> 5;
     region_append(want && !heavy, v, st.near_buf + w * NEAR_REGION, &st.near_n[w], NEAR_REGION,
-                  t.flush, t.qn, t.qn_count, a.n, &a.ctl->err);
+                  t.flush, t.qn, t.qn_count, a.n, &a.ctl->err,
+                  t.nostamp ? a.stamp_near : nullptr, t.tag_next);
     if (heavy) {
         uint32_t nc = (deg + CHUNK - 1) / CHUNK;
         uint32_t base = atomicAdd(t.hqn_count, nc);
@@ -371,14 +386,18 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                 atomicOr(&t.nbm[v >> 5], 1u << (v & 31));
                 dn[u] = true;
             }
+        } else if (nd[u] < t.T && t.nostamp) {
+            // ids at or above n_big cannot be hubs: no look at the row
+            if (v < a.n_big) {
+                const uint32_t r0 = a.row_ptr[v];
+                deg[u] = (a.lend ? a.lend[v] : a.row_ptr[v + 1]) - r0;
+            }
+            to_near[u] = deg[u] < HEAVY_DEG ||     // hubs join the chunk queue once
+                         atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
         } else if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v];                           // independent of the exchange
             uint32_t r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
-            // with local rounds a staged vertex may be relaxed this very
-            // iteration: the stamp exchange releases the label (the local
-            // reader acquire-exchanges the stamp, then reads the label)
-            to_near[u] = (a.local_rounds ? exch_release(&a.stamp_near[v], t.tag_next)
-                                         : atomicExch(&a.stamp_near[v], t.tag_next)) != t.tag_next;
+            to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
             cand[u] = true;      // bounds far_min
@@ -586,6 +605,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         uint32_t *bm_in = hp ? a.bbm : ((it & 1) ? a.nbm1 : a.nbm0);
         t.dense = push_dense;
         t.nbm = (it & 1) ? a.nbm0 : a.nbm1;
+        t.nostamp = a.local_rounds != 0 && !hp;
+        t.nostamp_stamp = a.stamp_near;
         // arcs relaxed by this iteration: all; light ones while a band
         // iterates under the split; heavy ones in the band's closing pass
         const uint32_t wlo = hp ? a.delta : 0u;
@@ -674,7 +695,6 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             // Warp-local rounds: each warp relaxes the vertices it staged
             // itself, a hop per round, with no block barrier between hops.
             const uint32_t wib = threadIdx.x >> 5;
-            const uint32_t tag_cur = t.tag_next - 1;
             t.flush = false;            // the loop below indexes into the region
             uint32_t *region = st.near_buf + wib * NEAR_REGION;
             uint32_t lo = 0;
@@ -689,13 +709,13 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                     uint64_t lab = INF64;
                     if (has) {
                         u = region[i];
-                        // row offsets are read-only: issued before the exchange,
-                        // they overlap it, and the arc loads then overlap the
-                        // label load (one dependent round trip less per hop)
+                        // row offsets and the label in one round trip: every
+                        // later improvement of u appends u again (to the
+                        // improving warp's region), so the current label is
+                        // all a round needs
                         s = a.row_ptr[u];
                         const uint32_t r1 = a.row_ptr[u + 1];
                         const uint32_t le = a.lend ? a.lend[u] : r1;
-                        exch_acquire(&a.stamp_near[u], tag_cur);   // later improvements re-push u
                         deg = le - s;
                         hdeg = a.lend ? r1 - le : r1 - s;
                         lab = sssp_label<NARROW>(a, u);
@@ -824,6 +844,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.flush = true;
         u.dense = a.dense;
         u.nbm = (its & 1) ? a.nbm1 : a.nbm0;
+        u.nostamp = false;             // the split visits each vertex once
+        u.nostamp_stamp = a.stamp_near;
         // the far pile, or with the far scan every vertex (coalesced labels)
         const uint32_t n_split = a.far_scan ? a.n : nf;
         // SPLIT_ILP chunks of 32 per warp step, their loads issued together.
