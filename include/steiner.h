@@ -237,8 +237,10 @@ int steiner_serve_stop(steiner_graph_t g);
  * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds, "batch_admitted"
  * (queries admitted into slots), "batch_admitted_busy" (of those, the
  * ones admitted while other slots were still on the device) and
- * "batch_tail_batches" (retirements whose tails ran batched); "batch_reset"
- * clears the timers and counters).  It returns -1 for an unknown key.
+ * "batch_tail_batches" (retirements whose tails ran batched) and
+ * "batch_narrow_reruns" (queries answered by the single-query path because
+ * a distance outgrew the engine's 32-bit labels); "batch_reset" clears the
+ * timers).  It returns -1 for an unknown key.
  */
 int steiner_set_param(steiner_graph_t g, const char *key, int64_t value);
 int64_t steiner_get_param(steiner_graph_t g, const char *key);

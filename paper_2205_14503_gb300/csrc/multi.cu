@@ -5,7 +5,10 @@
 // the same tie rules); what changes is how the work of up to 64 queries is
 // shared:
 //  * labels are vertex-major, label[v * 64 + q], so relaxing one arc for all
-//    pending slots is one contiguous 512-byte run of atomics;
+//    pending slots is one contiguous 256-byte run of atomics; a label is 32
+//    bits, (distance << b) | rank with b the bits of the slot's largest rank
+//    (ordered by (distance, rank) as the 64-bit form), and a slot whose
+//    distances do not fit is answered by the single-query path instead;
 //  * a frontier entry is a vertex; nmask[v] says which slots must relax
 //    v's arcs, so a CSR row is read once for all of them;
 //  * each slot has its own near/far threshold T[q] and far accounting, so a
@@ -35,7 +38,7 @@ struct MqArgs {
     const uint32_t *__restrict__ row_ptr;
     const uint2 *__restrict__ adj;
     uint32_t n;
-    uint64_t *label;
+    uint32_t *label;
     unsigned long long *nmask, *fmask;
     uint32_t *stamp_near, *in_far;
     uint32_t *q0, *q1;
@@ -77,7 +80,14 @@ struct MqStage {
     uint32_t fmin[MQ_SLOTS];               // far-distance minimum of this segment
     int32_t fpend[MQ_SLOTS];               // change of far_pending in this segment
     unsigned long long mag[MQ_SLOTS + 1];  // ceil(2^40 / c) for c = 2..64 (divmod by c)
+    uint32_t lshift[MQ_SLOTS];             // rank bits of each slot's labels
 };
+
+// Slot q's label of v in the 64-bit form (dist << 32) | rank.
+__device__ __forceinline__ uint64_t mq_label(const uint32_t *label, uint64_t v, uint32_t q,
+                                             uint32_t shift) {
+    return widen_label(ldcg_u32(&label[v * MQ_SLOTS + q]), shift);
+}
 
 struct MqTargets {
     uint32_t *qn, *qn_count;
@@ -203,7 +213,8 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
                                          const uint64_t (&lab)[MQ_ILP],
                                          const bool (&heavy)[MQ_ILP],
                                          unsigned long long &attempts,
-                                         unsigned long long &improved) {
+                                         unsigned long long &improved,
+                                         unsigned long long &narrow_miss) {
     uint2 e[MQ_ILP];
 #pragma unroll
     for (int i = 0; i < MQ_ILP; ++i) {
@@ -220,14 +231,16 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
         if (heavy[i] ? e[i].y < a.delta : (a.defer && e[i].y >= a.delta)) continue;
         ++attempts;
         nd[i] = (lab[i] >> 32) + (uint64_t)e[i].y;
-        if (nd[i] < INF32) {
+        const uint32_t sh = st.lshift[qs[i]];
+        if (nd[i] > (uint64_t)((1ull << (32 - sh)) - 2)) {
+            narrow_miss |= 1ull << qs[i];        // the slot is answered by the single-query path
+        } else {
             // read first: most proposals do not improve, and a load costs far
             // less L2 throughput than an atomic
-            uint64_t nl = (nd[i] << 32) | (lab[i] & 0xFFFFFFFFull);
-            uint64_t *dst = &a.label[(uint64_t)e[i].x * MQ_SLOTS + qs[i]];
-            if (nl < ldcg_u64(dst)) {
-                uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(dst),
-                                         (unsigned long long)nl);
+            const uint32_t nl = ((uint32_t)nd[i] << sh) | (uint32_t)lab[i];
+            uint32_t *dst = &a.label[(uint64_t)e[i].x * MQ_SLOTS + qs[i]];
+            if (nl < ldcg_u32(dst)) {
+                const uint32_t old = atomicMin(dst, nl);
                 imp[i] = nl < old;
             }
         }
@@ -275,7 +288,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const bool first = gtid == 0;
-    unsigned long long attempts = 0, improved = 0;
+    unsigned long long attempts = 0, improved = 0, narrow_miss = 0;
     uint32_t it = ldcg_u32(&ctl->it), fc = ldcg_u32(&ctl->fc);
     unsigned long long infl = __ldcg(&ctl->inflight) & ~__ldcg(&ctl->converged);
     unsigned long long conv_total = 0;
@@ -283,7 +296,10 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
     unsigned long long H = __ldcg(&ctl->hpass) & infl;
     unsigned long long hp_done = __ldcg(&ctl->hp_done);
     uint32_t bc = ldcg_u32(&ctl->blist);
-    if (threadIdx.x < MQ_SLOTS) st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
+    if (threadIdx.x < MQ_SLOTS) {
+        st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
+        st.lshift[threadIdx.x] = ldcg_u32(&ctl->lshift[threadIdx.x]);
+    }
     if (threadIdx.x <= MQ_SLOTS) {
         const uint32_t c = threadIdx.x;
         st.mag[c] = c > 1 ? ((1ull << 40) + c - 1) / c : 0ull;
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                         const uint32_t tq = lane & ((1u << gsh) - 1u), aoff = lane >> gsh;
                         const bool tok = tq < cw;
                         const uint32_t q = tok ? nth_bit64(Mw, tq) : 0u;
-                        const uint64_t lab = tok ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q]) : INF64;
+                        const uint64_t lab = tok ? mq_label(a.label, uw, q, st.lshift[q]) : INF64;
                         for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP * A) {
                             bool valid[MQ_ILP], heavy[MQ_ILP];
                             uint32_t arc[MQ_ILP], qs[MQ_ILP];
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                                 qs[k] = q;
                                 labs[k] = lab;
                             }
-                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
+                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved, narrow_miss);
                         }
                     } else {
                         // 33..64 slots: each lane takes slots lane and lane + 32
@@ -481,8 +497,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                         const bool tok1 = t1 < cw;
                         const uint32_t q0 = cw == MQ_SLOTS ? lane : nth_bit64(Mw, lane);
                         const uint32_t q1 = tok1 ? (cw == MQ_SLOTS ? t1 : nth_bit64(Mw, t1)) : 0u;
-                        const uint64_t lab0 = ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q0]);
-                        const uint64_t lab1 = tok1 ? ldcg_u64(&a.label[(uint64_t)uw * MQ_SLOTS + q1]) : INF64;
+                        const uint64_t lab0 = mq_label(a.label, uw, q0, st.lshift[q0]);
+                        const uint64_t lab1 = tok1 ? mq_label(a.label, uw, q1, st.lshift[q1]) : INF64;
                         for (uint32_t j0 = jlo; j0 <= jhi; j0 += MQ_ILP / 2) {
                             bool valid[MQ_ILP], heavy[MQ_ILP];
                             uint32_t arc[MQ_ILP], qs[MQ_ILP];
@@ -499,7 +515,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                                 qs[k] = second ? q1 : q0;
                                 labs[k] = second ? lab1 : lab0;
                             }
-                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved);
+                            mq_relax(a, st, t, valid, arc, qs, labs, heavy, attempts, improved, narrow_miss);
                         }
                     }
                 }
@@ -584,7 +600,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
             unsigned long long MS = M & S, moved = 0, dropped = 0;
             for (unsigned long long m = MS; m; m &= m - 1) {
                 uint32_t q = __ffsll((long long)m) - 1;
-                uint64_t d = ldcg_u64(&a.label[(uint64_t)v * MQ_SLOTS + q]) >> 32;
+                uint64_t d = mq_label(a.label, v, q, st.lshift[q]) >> 32;
                 if (d < st.T[q]) {
                     dropped |= 1ull << q;                  // settled while parked
                 } else if (d < st.Tnew[q]) {
@@ -639,6 +655,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
         atomicAdd(&ctl->relax_attempts, attempts);
         atomicAdd(&ctl->relax_improved, improved);
     }
+    narrow_miss = warp_or64(narrow_miss);
+    if (lane == 0 && narrow_miss) atomicOr(&ctl->slot_narrow, narrow_miss);
     if (first) {
         ctl->it = it;
         ctl->fc = fc;
@@ -657,22 +675,22 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
 // admission of one slot: clear its label/pred column, seed it
 // ---------------------------------------------------------------------------
 
-__global__ void mq_clear_column_kernel(uint32_t n, uint64_t *label, uint32_t *pred, uint32_t q) {
+__global__ void mq_clear_column_kernel(uint32_t n, uint32_t *label, uint32_t *pred, uint32_t q) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        label[(uint64_t)v * MQ_SLOTS + q] = INF64;
+        label[(uint64_t)v * MQ_SLOTS + q] = INF32;
         pred[(uint64_t)v * MQ_SLOTS + q] = INF32;
     }
 }
 
 // Clears the label/pred columns of every slot in `mask` with row-wide,
 // coalesced stores (one thread per (vertex, slot) element).
-__global__ void mq_clear_rows_kernel(uint32_t n, uint64_t *label, uint32_t *pred,
+__global__ void mq_clear_rows_kernel(uint32_t n, uint32_t *label, uint32_t *pred,
                                      unsigned long long mask) {
     uint64_t total = (uint64_t)n * MQ_SLOTS;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         if ((mask >> (i & (MQ_SLOTS - 1))) & 1ull) {
-            label[i] = INF64;
+            label[i] = INF32;
             pred[i] = INF32;
         }
     }
@@ -686,6 +704,10 @@ __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n,
     const uint32_t it = ctl->it;
     const unsigned long long bit = 1ull << q;
     if (r == 0) {
+        uint32_t b = 1;
+        while (b < 31 && (1u << b) < k) ++b;
+        ctl->lshift[q] = b;
+        ctl->slot_narrow &= ~bit;
         ctl->T[q] = delta;
         ctl->fmin[0][q] = INF32;
         ctl->fmin[1][q] = INF32;
@@ -697,7 +719,7 @@ __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n,
     }
     if (r >= k) return;
     uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
-    m.label[(uint64_t)s * MQ_SLOTS + q] = (uint64_t)r;
+    m.label[(uint64_t)s * MQ_SLOTS + q] = r;          // distance 0, rank r
     m.pred[(uint64_t)s * MQ_SLOTS + q] = SEED_ARC;
     atomicOr(&m.nmask[s], bit);
     uint32_t tag = m.base_near + it;
@@ -720,7 +742,8 @@ struct MqScanArgs {
     const uint64_t *__restrict__ heavy_chunks;
     uint32_t n_heavy_chunks;
     uint32_t n;
-    const uint64_t *label;
+    const uint32_t *label;
+    const uint32_t *lshift;          // rank bits of each slot's labels
     uint32_t *pred;
     uint64_t *const *pairtab;
     const uint32_t *k;
@@ -792,6 +815,7 @@ constexpr int SCAN_PAIR_ILP = 2;   // arcs in flight per lane in the slot-pair m
 // sizes loaded once.
 struct LaneSlots {
     uint32_t q0, k0, k1;
+    uint32_t sh0, sh1;      // rank bits of the slots' labels
     bool h0, h1;
     uint64_t *t0, *t1;
 };
@@ -810,27 +834,27 @@ __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, const LaneSlots
                                             unsigned long long &overflow) {
     const uint32_t lane = lane_id();
     const uint32_t cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, rs);
-    const uint64_t *lrow = &a.label[(uint64_t)v * MQ_SLOTS];
+    const uint32_t *lrow = &a.label[(uint64_t)v * MQ_SLOTS];
     if (cnt > 32) {
         if (!ls.h0 && !ls.h1) return;
-        const ulonglong2 lv = __ldg(reinterpret_cast<const ulonglong2 *>(&lrow[ls.q0]));
-        ScanSlot r0 = mq_row_slot(a, v, ls.q0, ls.t0, ls.k0, lv.x);
-        ScanSlot r1 = mq_row_slot(a, v, ls.q0 + 1, ls.t1, ls.k1, lv.y);
+        const uint2 lv = __ldg(reinterpret_cast<const uint2 *>(&lrow[ls.q0]));
+        ScanSlot r0 = mq_row_slot(a, v, ls.q0, ls.t0, ls.k0, widen_label(lv.x, ls.sh0));
+        ScanSlot r1 = mq_row_slot(a, v, ls.q0 + 1, ls.t1, ls.k1, widen_label(lv.y, ls.sh1));
         for (uint32_t j0 = s0; j0 < s1; j0 += SCAN_PAIR_ILP) {
             uint2 e[SCAN_PAIR_ILP];
-            ulonglong2 lu[SCAN_PAIR_ILP];
+            uint2 lu[SCAN_PAIR_ILP];
 #pragma unroll
             for (int k = 0; k < SCAN_PAIR_ILP; ++k)
                 if (j0 + k < s1) e[k] = __ldg(&a.adj[j0 + k]);
 #pragma unroll
             for (int k = 0; k < SCAN_PAIR_ILP; ++k)
                 if (j0 + k < s1)
-                    lu[k] = __ldg(reinterpret_cast<const ulonglong2 *>(&a.label[(uint64_t)e[k].x * MQ_SLOTS + ls.q0]));
+                    lu[k] = __ldg(reinterpret_cast<const uint2 *>(&a.label[(uint64_t)e[k].x * MQ_SLOTS + ls.q0]));
 #pragma unroll
             for (int k = 0; k < SCAN_PAIR_ILP; ++k) {
                 if (j0 + k >= s1) break;
-                if (ls.h0) mq_scan_eval(r0, j0 + k, e[k], lu[k].x, cbase, overflow);
-                if (ls.h1) mq_scan_eval(r1, j0 + k, e[k], lu[k].y, cbase, overflow);
+                if (ls.h0) mq_scan_eval(r0, j0 + k, e[k], widen_label(lu[k].x, ls.sh0), cbase, overflow);
+                if (ls.h1) mq_scan_eval(r1, j0 + k, e[k], widen_label(lu[k].y, ls.sh1), cbase, overflow);
             }
         }
         if (ls.h0) mq_store_pred(a, v, r0, whole_row);
@@ -840,15 +864,14 @@ __device__ __forceinline__ void mq_scan_row(const MqScanArgs &a, const LaneSlots
     const uint32_t g = 1u << gsh, apr = 32 >> gsh, grp = lane >> gsh;
     const bool has_slot = ls.h0;
     ScanSlot r = mq_row_slot(a, v, ls.q0, ls.t0, ls.k0,
-                             has_slot ? __ldg(reinterpret_cast<const unsigned long long *>(&lrow[ls.q0]))
-                                      : INF64);
+                             has_slot ? widen_label(__ldg(&lrow[ls.q0]), ls.sh0) : INF64);
     for (uint32_t j0 = s0; j0 < s1; j0 += apr * 4) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t arc = j0 + k * apr + grp;
             if (has_slot && arc < s1) {
                 uint2 e = __ldg(&a.adj[arc]);
-                uint64_t lu = __ldg(reinterpret_cast<const unsigned long long *>(&a.label[(uint64_t)e.x * MQ_SLOTS + ls.q0]));
+                uint64_t lu = widen_label(__ldg(&a.label[(uint64_t)e.x * MQ_SLOTS + ls.q0]), ls.sh0);
                 mq_scan_eval(r, arc, e, lu, cbase, overflow);
             }
         }
@@ -879,6 +902,8 @@ __global__ void __launch_bounds__(256, 5) mq_scan_kernel(MqScanArgs a) {
     ls.k0 = ls.h0 ? a.k[ls.q0] : 0;
     ls.t1 = ls.h1 ? a.pairtab[ls.q0 + 1] : nullptr;
     ls.k1 = ls.h1 ? a.k[ls.q0 + 1] : 0;
+    ls.sh0 = ls.h0 ? a.lshift[ls.q0] : 1;
+    ls.sh1 = ls.h1 ? a.lshift[ls.q0 + 1] : 1;
     const uint32_t n_batches = (a.n + 31) / 32;
     const uint32_t n_work = a.n_heavy_chunks + n_batches;
     unsigned long long overflow = 0;
@@ -921,7 +946,7 @@ cudaError_t mq_alloc(const DevGraph &g, MqState &m, cudaStream_t s) {
     m.n = n;
     cudaError_t e;
 #define MA(ptr, cnt) if ((e = mq_dalloc(ptr, cnt)) != cudaSuccess) return e
-    MA(m.label, (uint64_t)n * MQ_SLOTS);
+    MA(m.label, (uint64_t)n * MQ_SLOTS);      // 32-bit labels
     MA(m.pred, (uint64_t)n * MQ_SLOTS);
     MA(m.nmask, n);
     MA(m.fmask, n);
@@ -1049,6 +1074,7 @@ cudaError_t mq_launch_scan(const DevGraph &g, MqState &m, unsigned long long slo
     a.n_heavy_chunks = g.n_heavy_chunks;
     a.n = g.n;
     a.label = m.label;
+    a.lshift = m.ctl->lshift;
     a.pred = m.pred;
     a.pairtab = m.d_pairtab;
     a.k = m.d_k;

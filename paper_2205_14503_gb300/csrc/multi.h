@@ -3,7 +3,7 @@
 // Up to MQ_SLOTS queries ("slots") run in one persistent kernel over the
 // resident graph.  Per-vertex state is vertex-major: the labels of vertex v
 // for all slots are label[v * MQ_SLOTS + q], so relaxing one arc for every
-// pending slot touches one contiguous 512-byte run, and each CSR row is
+// pending slot touches one contiguous 256-byte run (32-bit labels), and each CSR row is
 // read once per frontier visit for all the slots that need it (a 64-bit
 // mask per vertex says which).
 #pragma once
@@ -51,11 +51,13 @@ struct MqControl {
     unsigned long long hpass;           // slots whose heavy-arc pass runs in the next iteration
     uint32_t blist;                     // band list receiving appends (rotates over 3)
     uint32_t bcount[3];
+    uint32_t lshift[MQ_SLOTS];          // rank bits of each slot's 32-bit labels
+    unsigned long long slot_narrow;     // slots with a distance too large for their labels
 };
 
 struct MqState {
     uint32_t n = 0;
-    uint64_t *label = nullptr;              // n * MQ_SLOTS
+    uint32_t *label = nullptr;              // n * MQ_SLOTS: (dist << lshift[q]) | rank
     uint32_t *pred = nullptr;               // n * MQ_SLOTS (pred arc per slot)
     unsigned long long *nmask = nullptr;    // n
     unsigned long long *fmask = nullptr;    // n

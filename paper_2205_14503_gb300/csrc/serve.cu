@@ -149,6 +149,10 @@ struct BatchEngine {
     // pass, seeds them and waits once.  Caller holds the graph mutex.
     unsigned long long staged = 0;
     std::vector<std::vector<int32_t>> staged_seeds = std::vector<std::vector<int32_t>>(MQ_SLOTS);
+    // each busy slot's sorted seeds, kept until release: a slot whose
+    // distances outgrow its 32-bit labels runs again as a single query
+    std::vector<std::vector<int32_t>> slot_seeds = std::vector<std::vector<int32_t>>(MQ_SLOTS);
+    uint64_t narrow_reruns = 0;
 
     int admit(int q, const std::vector<int32_t> &ss, uint64_t tag) {
         int rc = stage(q, ss, tag);
@@ -201,6 +205,7 @@ struct BatchEngine {
                                     cudaMemcpyHostToDevice, s);
         }
         staged_seeds[q] = ss;     // host copy lives until commit() has waited
+        slot_seeds[q] = ss;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(m.seeds[q], staged_seeds[q].data(), (size_t)k * 4,
                                 cudaMemcpyHostToDevice, s);
@@ -289,8 +294,9 @@ struct BatchEngine {
         int bq[MQ_SLOTS];
         uint32_t bk[MQ_SLOTS];
         int nb = 0;
+        const unsigned long long narrow = e == cudaSuccess ? h_ctl->slot_narrow : 0ull;
         if (e == cudaSuccess && batched_tails)
-            for (unsigned long long mm = mask; mm; mm &= mm - 1) {
+            for (unsigned long long mm = mask & ~narrow; mm; mm &= mm - 1) {
                 const int q = __builtin_ctzll(mm);
                 if (!((h_ctl->slot_overflow >> q) & 1ull) && slots[q].k > 1) {
                     bq[nb] = q;
@@ -307,6 +313,11 @@ struct BatchEngine {
             if (e != cudaSuccess) {
                 r.status = STEINER_ECUDA;
                 api_set_error(std::string("batched scan: ") + cudaGetErrorString(e));
+            } else if ((narrow >> q) & 1ull) {
+                // a distance outgrew the slot's 32-bit labels: the query runs
+                // alone through the single-query path (64-bit labels as needed)
+                ++narrow_reruns;
+                api_query_locked(G, slot_seeds[q].data(), slots[q].k, &r);
             } else if (batched && bi < nb && bq[bi] == q) {
                 r = bres[bi++];
             } else {
@@ -332,6 +343,7 @@ struct BatchEngine {
     }
 
     void release_slot(int q) {
+        slot_seeds[q].clear();
         used -= slots[q].bytes;
         slots[q] = SlotInfo();
         inflight &= ~(1ull << q);
@@ -373,6 +385,7 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_admitted_busy") return (int64_t)B->admitted_busy;
     if (k == "batch_tails") return B->batched_tails;
     if (k == "batch_tail_batches") return (int64_t)B->tail_batches;
+    if (k == "batch_narrow_reruns") return (int64_t)B->narrow_reruns;
     if (k == "batch_delta") return B->cur_delta();
     if (k == "batch_yield_div") return B->yield_div;
     if (k.rfind("batch_t", 0) == 0 && k.size() == 8 && B->h_ctl) return (int64_t)B->h_ctl->t_part[k[7] - '0'];

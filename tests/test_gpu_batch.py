@@ -238,3 +238,22 @@ def test_batched_tails_many_seeds_and_shared_vertices():
     _check(g, qs, out[1])
     for a, b in zip(out[1], out[0]):
         assert np.array_equal(a.edges, b.edges) and a.total == b.total
+
+
+def test_batch_labels_that_outgrow_32_bits():
+    """The engine keeps 32-bit labels, (distance << b) | rank with b the bits
+    of the slot's largest rank; a query whose distances do not fit (here a
+    path of weight-10^6 edges with up to 1000 seeds at one end: 10 rank bits
+    leave distances below about 4 * 10^6) is answered by the single-query
+    path, and every tree equals the oracle's."""
+    n = 4000
+    rng = np.random.default_rng(9)
+    g = wl.from_edges(n, np.arange(n - 1), np.arange(1, n), rng.integers(900_000, 1_000_001, n - 1))
+    qs = [np.arange(1000, dtype=np.int32), np.array([0, 5, 17]), np.arange(0, 600, 2),
+          np.array([10, 3990]), np.arange(200, dtype=np.int32)]
+    with st.SteinerGraph(g) as Gd:
+        rc, res = Gd.query_batch(qs)
+        reruns = Gd.get_param("batch_narrow_reruns")
+    assert rc == st.STEINER_OK
+    assert reruns >= 1
+    _check(g, qs, res)
