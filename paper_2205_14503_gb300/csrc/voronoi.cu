@@ -331,10 +331,10 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
         if (valid[u]) e[u] = stream ? __ldcs(&a.adj[arc[u]]) : __ldg(&a.adj[arc[u]]);
     }
     uint64_t nd[ILP];
-    bool imp[ILP];
+    bool imp[ILP], fr[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-        imp[u] = false;
+        imp[u] = fr[u] = false;
         nd[u] = INF32;
         if (valid[u] && e[u].y >= wlo && e[u].y < whi) {
             ++attempts;
@@ -346,8 +346,15 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                     const uint32_t nl = ((uint32_t)nd[u] << a.lshift) | (uint32_t)lab[u];
                     if (!precheck || nl < ldcg_u32(&a.label32[e[u].x])) {
                         ++atomics;
-                        const uint32_t old = atomicMin(&a.label32[e[u].x], nl);
-                        imp[u] = nl < old;
+                        if (a.far_scan && nd[u] >= t.T) {
+                            // a far proposal needs no answer (nothing is queued
+                            // for it): a fire-and-forget reduction
+                            atomicMin(&a.label32[e[u].x], nl);
+                            fr[u] = true;
+                        } else {
+                            const uint32_t old = atomicMin(&a.label32[e[u].x], nl);
+                            imp[u] = nl < old;
+                        }
                     }
                 }
             } else if (nd[u] < INF32) {
@@ -355,20 +362,27 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
                 uint64_t nl = (nd[u] << 32) | (lab[u] & 0xFFFFFFFFull);
                 if (!precheck || nl < ldcg_u64(&a.label[e[u].x])) {
                     ++atomics;
-                    uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
-                                             (unsigned long long)nl);
-                    imp[u] = nl < old;
+                    if (a.far_scan && nd[u] >= t.T) {
+                        atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
+                                  (unsigned long long)nl);
+                        fr[u] = true;
+                    } else {
+                        uint64_t old = atomicMin(reinterpret_cast<unsigned long long *>(&a.label[e[u].x]),
+                                                 (unsigned long long)nl);
+                        imp[u] = nl < old;
+                    }
                 }
             }
         }
     }
     // rounds that improve nothing skip the append machinery
-    if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3])) return;
+    if (!__any_sync(FULL, imp[0] | imp[1] | imp[2] | imp[3] | fr[0] | fr[1] | fr[2] | fr[3])) return;
     bool to_near[ILP], to_far[ILP], cand[ILP], dn[ILP];
     uint32_t deg[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-        to_near[u] = to_far[u] = cand[u] = dn[u] = false;
+        to_near[u] = to_far[u] = dn[u] = false;
+        cand[u] = fr[u];         // a fire-and-forget far proposal still bounds far_min
         deg[u] = 0;
         if (!imp[u]) continue;
         ++improved;
@@ -955,10 +969,9 @@ __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
         }
         if (cell) cell[v] = seeds[(uint32_t)lab];
         if (dist) dist[v] = (uint32_t)(lab >> 32);
-        if (pred) {
-            uint32_t pa = pred_arc[u];
-            pred[v] = pa == SEED_ARC ? (int32_t)v
-                                     : (pa == INF32 ? -1 : (int32_t)caller_id(orig_of, adj[pa].x));
+        if (pred) {               // the scan left the predecessor's caller id
+            const uint32_t pc = pred_arc[u];
+            pred[v] = pc == SEED_ARC ? (int32_t)v : (pc == INF32 ? -1 : (int32_t)pc);
         }
     }
 }
