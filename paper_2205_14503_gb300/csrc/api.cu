@@ -754,7 +754,6 @@ int api_run_tail(steiner_graph *G, uint64_t *pairtab, uint32_t *pred_base, uint3
     v.pairtab = pairtab;
     v.pred_arc = pred_base;
     v.pred_stride = pred_stride;
-    v.pred_vertex = false;            // the multi-query scan records pred arcs
     cudaStream_t s = G->stream;
     CK(cudaMemsetAsync(v.ctl, 0, sizeof(Control), s));
     CK(launch_compact_pairs(v, k, s));

@@ -2,7 +2,9 @@
 //
 //  * pred (Algorithm 2 Step 1's predecessor state; Algorithm 4 line 8):
 //    pred(v) = the smallest-id neighbour u with cell(u) = cell(v) and
-//    d1(u) + d(u,v) = d1(v): an atomicMin of u's caller id into pred[v].
+//    d1(u) + d(u,v) = d1(v).  Rows are sorted by neighbour id, so the
+//    smallest arc index in v's row is the smallest id: atomicMin on the
+//    arc index.
 //  * bridges (Algorithm 2 Step 2; Algorithm 5): for an arc u -> v with
 //    rank(cell u) < rank(cell v), b = d1(u) + d(u,v) + d1(v); the pair's
 //    table slot keeps min((b << 32) | arc) by 64-bit atomicMin, which is
@@ -12,13 +14,6 @@
 //
 // The pair table is a direct-address table over the k(k-1)/2 seed pairs
 // (an upper-triangle index, i.e. a collision-free hash of the pair).
-//
-// Every undirected edge {v, u} is taken once, from the row of its smaller
-// internal id v (the other arc is skipped after its record is read), so
-// half the random head-label loads of an arc-by-arc scan go: the edge
-// serves pred of either end, and a bridge leaving u's cell (u -> v is the
-// arc of the key) looks up the caller's index of the reverse arc by binary
-// search in u's row, only when the bridge can beat or tie the table.
 //
 // Load balance: vertices with degree < HEAVY_DEG are processed 32 per warp
 // with their arcs flattened over the lanes (labels of 32 consecutive
@@ -37,7 +32,7 @@ struct ScanArgs {
     const uint64_t *label;
     const uint32_t *label32;         // narrow labels (the narrow kernel)
     uint32_t lshift;
-    uint32_t *pred;                  // smallest caller id of a tight same-cell neighbour
+    uint32_t *pred_arc;
     uint64_t *pairtab;
     uint32_t k;
     bool pairs;
@@ -53,66 +48,36 @@ __device__ __forceinline__ uint64_t scan_label(const ScanArgs &a, uint32_t v) {
     return __ldg(reinterpret_cast<const unsigned long long *>(&a.label[v]));
 }
 
-// Caller's index of the arc u -> v: binary search in u's row, whose
-// neighbours are in ascending caller id (the caller's order is kept).
-__device__ __forceinline__ uint32_t reverse_caller_arc(const ScanArgs &a, uint32_t u, uint32_t v) {
-    const uint32_t rs = a.row_ptr[u];
-    uint32_t lo = rs, hi = a.row_ptr[u + 1];
-    const uint32_t target = caller_id(a.orig_of, v);
-    while (hi - lo > 1) {
-        const uint32_t mid = lo + (hi - lo) / 2;
-        if (caller_id(a.orig_of, a.adj[mid].x) <= target) lo = mid; else hi = mid;
-    }
-    return caller_arc_base(a.orig_of, a.orig_row_ptr, u, rs) + lo;
-}
-
-// Arc `arc` of row v: the edge {v, u} when v < u (internal ids).  A bridge
-// key carries the caller's index of the arc leaving the smaller-rank cell:
-// cbase + arc for v -> u (cbase: the caller's row start of v minus v's
-// internal row start, taken once per row), the reverse arc's otherwise, so
-// ties between equal bridges break on the caller's CSR order whatever the
-// internal vertex order.
+// Arc `arc` of row v.  The bridge key carries the caller's arc index,
+// cbase + arc (cbase: the caller's row start of v minus v's internal row
+// start, taken once per row), so ties between equal bridges break on the
+// caller's CSR order whatever the internal vertex order.
 template <bool NARROW>
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
                                          uint32_t cbase, uint32_t arc, bool &overflow) {
     if (!valid) return;
-    const uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
-    const uint32_t u = e.x;
-    if (u < v) return;                       // the edge is taken from u's row
-    const uint64_t lu = scan_label<NARROW>(a, u);
+    uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
+    uint64_t lu = scan_label<NARROW>(a, e.x);
     if (lv == INF64 || lu == INF64) {
         // a reached vertex next to an unreached one: its true distance is
         // finite but did not fit below 2^32 - 1
         if (lv != lu) overflow = true;
         return;
     }
-    const uint32_t cv = (uint32_t)lv, cu = (uint32_t)lu;
-    const uint64_t dv = lv >> 32, du = lu >> 32;
+    uint32_t cv = (uint32_t)lv, cu = (uint32_t)lu;
+    uint64_t dv = lv >> 32, du = lu >> 32;
     if (cu == cv) {
-        // at most one direction is tight (weights are at least 1)
-        if (du + e.y == dv) atomicMin(&a.pred[v], caller_id(a.orig_of, u));
-        else if (dv + e.y == du) atomicMin(&a.pred[u], caller_id(a.orig_of, v));
-    } else if (a.pairs) {
-        const uint64_t b = dv + e.y + du;
+        if (du + e.y == dv) atomicMin(&a.pred_arc[v], arc);
+    } else if (a.pairs && cv < cu) {
+        uint64_t b = dv + e.y + du;
         if (b >= INF32) {
             overflow = true;
             return;
         }
-        if (cv < cu) {
-            const uint64_t key = (b << 32) | (uint32_t)(cbase + arc);
-            uint64_t *slot = &a.pairtab[pair_slot(cv, cu, a.k)];
-            if (key < ldcg_u64(slot))
-                atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
-        } else {
-            uint64_t *slot = &a.pairtab[pair_slot(cu, cv, a.k)];
-            const uint64_t cur = ldcg_u64(slot);
-            if (b <= (cur >> 32)) {          // can beat or tie the table: find the arc
-                const uint64_t key = (b << 32) | reverse_caller_arc(a, u, v);
-                if (key < cur)
-                    atomicMin(reinterpret_cast<unsigned long long *>(slot),
-                              (unsigned long long)key);
-            }
-        }
+        uint64_t key = (b << 32) | (uint32_t)(cbase + arc);
+        uint64_t *slot = &a.pairtab[pair_slot(cv, cu, a.k)];
+        if (key < ldcg_u64(slot))
+            atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
     }
 }
 
@@ -275,7 +240,7 @@ cudaError_t launch_scan(const DevGraph &g, Workspace &ws, uint32_t k, bool pairs
     a.label = ws.label;
     a.label32 = ws.label32;
     a.lshift = ws.lshift;
-    a.pred = ws.pred_arc;
+    a.pred_arc = ws.pred_arc;
     a.pairtab = ws.pairtab;
     a.k = k;
     a.pairs = pairs && k > 1;

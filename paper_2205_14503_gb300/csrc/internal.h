@@ -111,12 +111,8 @@ struct Workspace {
     uint32_t *label32 = nullptr;
     uint32_t lshift = 0;
     bool narrow = false;
-    // pred of v at pred_arc[v * pred_stride]: the caller id of its
-    // predecessor (pred_vertex, the single-query scan) or the arc of the
-    // pred edge in v's row (the multi-query scan); SEED_ARC; INF32
-    uint32_t *pred_arc = nullptr;
-    uint32_t pred_stride = 1;
-    bool pred_vertex = true;
+    uint32_t *pred_arc = nullptr;   // arc of the pred edge in v's row; SEED_ARC; INF32
+    uint32_t pred_stride = 1;       // pred of v at pred_arc[v * pred_stride]
     uint32_t *stamp_near = nullptr;
     uint32_t *stamp_far = nullptr;
     uint32_t *stamp_band = nullptr;  // band-list membership tags

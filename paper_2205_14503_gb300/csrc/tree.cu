@@ -128,10 +128,8 @@ __device__ __forceinline__ void emit_edge(uint32_t a, uint32_t b, uint32_t w, ui
 
 // Two threads per MST pair: thread 0 emits the bridge and walks pred() from
 // the bridge's tail, thread 1 walks from its head.  Per hop the mark exchange
-// is issued beside the loads it does not depend on.  pred is either the
-// predecessor's caller id (pred_vertex; a pred edge is tight, so its weight
-// is the difference of the two distances) or the arc of the pred edge in
-// the vertex's row (its record gives the neighbour and the weight).
+// and the pred load are issued together, so a hop costs two dependent loads
+// (pred arc, then the arc's record) instead of three.
 __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
                               const uint32_t *__restrict__ orig_of,
                               const uint32_t *__restrict__ new_of,
@@ -139,13 +137,8 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
                               uint32_t n, const uint32_t *__restrict__ e_arc,
                               const uint32_t *__restrict__ e_mst,
                               const uint32_t *__restrict__ pred_arc, uint32_t pred_stride,
-                              bool pred_vertex, const uint64_t *__restrict__ label,
-                              const uint32_t *__restrict__ label32, uint32_t lshift,
                               uint32_t *mark, uint32_t tag, uint32_t nbits, uint64_t *key,
                               uint32_t *wout, uint32_t cap, Control *ctl) {
-    auto dist = [&](uint32_t x) -> uint32_t {
-        return label32 ? label32[x] >> lshift : (uint32_t)(label[x] >> 32);
-    };
     const uint32_t E = ldcg_u32(&ctl->n_pairs);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * E; t += gridDim.x * blockDim.x) {
         const uint32_t j = t >> 1, side = t & 1;
@@ -169,21 +162,6 @@ __global__ void expand_kernel(const uint32_t *__restrict__ row_ptr, const uint2 
             x = tail;
             emit_edge(caller_id(orig_of, x), caller_id(orig_of, e.x), e.y, nbits, key, wout, cap,
                       ctl);
-        }
-        if (pred_vertex) {
-            uint32_t dx = dist(x);
-            for (uint32_t steps = 0; steps < n; ++steps) {
-                const uint32_t pc = pred_arc[(uint64_t)x * pred_stride];
-                if (pc == SEED_ARC || pc == INF32) break;
-                const uint32_t old = atomicExch(&mark[x], tag);
-                const uint32_t y = internal_id(new_of, pc);   // independent of the exchange
-                const uint32_t dy = dist(y);
-                if (old == tag) break;           // the rest of the chain is another walker's
-                emit_edge(caller_id(orig_of, x), pc, dx - dy, nbits, key, wout, cap, ctl);
-                x = y;
-                dx = dy;
-            }
-            continue;
         }
         for (uint32_t steps = 0; steps < n; ++steps) {
             uint32_t pa = pred_arc[(uint64_t)x * pred_stride];
@@ -358,9 +336,7 @@ cudaError_t launch_tree(const DevGraph &g, Workspace &ws, uint32_t k, uint32_t t
     uint32_t blocks = (uint32_t)std::min<uint64_t>((2 * slots + 255) / 256, (uint64_t)current_sm_count() * 8);
     expand_kernel<<<blocks, 256, 0, s>>>(g.row_ptr, g.adj, g.orig_of, g.new_of, g.orig_row_ptr,
                                          g.n, ws.e_arc, ws.e_mst, ws.pred_arc,
-                                         ws.pred_stride, ws.pred_vertex, ws.label,
-                                         ws.narrow ? ws.label32 : nullptr, ws.lshift, ws.mark, tag,
-                                         n_bits, ws.tree_key,
+                                         ws.pred_stride, ws.mark, tag, n_bits, ws.tree_key,
                                          ws.tree_w, ws.tree_cap, ws.ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

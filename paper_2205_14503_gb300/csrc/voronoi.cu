@@ -969,9 +969,10 @@ __global__ void export_kernel(uint32_t n, const uint2 *__restrict__ adj,
         }
         if (cell) cell[v] = seeds[(uint32_t)lab];
         if (dist) dist[v] = (uint32_t)(lab >> 32);
-        if (pred) {               // the scan left the predecessor's caller id
-            const uint32_t pc = pred_arc[u];
-            pred[v] = pc == SEED_ARC ? (int32_t)v : (pc == INF32 ? -1 : (int32_t)pc);
+        if (pred) {
+            uint32_t pa = pred_arc[u];
+            pred[v] = pa == SEED_ARC ? (int32_t)v
+                                     : (pa == INF32 ? -1 : (int32_t)caller_id(orig_of, adj[pa].x));
         }
     }
 }
