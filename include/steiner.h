@@ -223,6 +223,12 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  bands: -1 (default) chooses, 0 keeps a pile of them
  *                  (one stamp exchange and queue slot per improvement),
  *                  1 scans every label at the split instead
+ *   "pull"         form of a band's heavy-arc pass (with the far scan):
+ *                  1 (default) chooses per band the form that reads fewer
+ *                  arcs, 0 pushes the heavy arcs of the band's vertices,
+ *                  2 pulls: every vertex still at or above the threshold
+ *                  reads its own heavy arcs and takes the best proposal
+ *                  from the settled vertices at their other ends
  *   "label_bits"   width of the Voronoi labels: 0 (default) chooses per
  *                  query, 32 or 64 force it.  A 32-bit label holds
  *                  (distance << b) | rank with b the bits of the largest
@@ -230,7 +236,8 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  with 64-bit labels, so results never depend on the width
  * steiner_get_param also reads "sssp_max_blocks", "sm_count",
  * "heavy_chunks", "label_bits_last" (the width the last query ended with),
- * "narrow_reruns" (queries rerun with 64-bit labels) and the multi-query
+ * "narrow_reruns" (queries rerun with 64-bit labels), "pull_passes_last"
+ * (heavy-arc passes of the last query run in the pull form) and the multi-query
  * engine's tracing counters
  * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
  * microseconds, "batch_launches", "batch_iterations", "batch_items",

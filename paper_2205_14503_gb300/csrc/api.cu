@@ -81,6 +81,11 @@ struct steiner_graph {
     // Dense frontiers (bitmaps for large frontiers and band lists) wherever
     // the far scan runs without local rounds; 0 turns them off.
     uint32_t dense = 1;
+    // Heavy-arc passes of the light/heavy split (with the far scan): 1
+    // runs each in the push or the pull form, whichever reads fewer arcs;
+    // 0 always pushes, 2 always pulls.
+    uint32_t pull = 1;
+    uint32_t last_pulls = 0;
     uint32_t narrow_fail_dbits = 0;   // most distance bits a narrow attempt ran out of
     uint32_t last_label_bits = 0;
     uint64_t narrow_reruns = 0;
@@ -243,7 +248,7 @@ int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool ful
     static const bool trace = getenv("STEINER_TRACE") != nullptr;
     const uint32_t dense = (G->dense && far_scan && G->local_rounds == 0) ? 1u : 0u;
     SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
-                 ws.epoch_band, far_scan, trace ? 1u : 0u, dense};
+                 ws.epoch_band, far_scan, trace ? 1u : 0u, dense, far_scan ? G->pull : 0u};
     CK(cudaEventRecord(G->ev[0], s));
     CK(ensure_partition(G, G->delta));
     CK(launch_init(G->g, ws, k, G->delta, s));
@@ -271,6 +276,7 @@ int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool ful
         ms[5] = (float)launches;
     }
     advance_epochs(ws, *G->h_ctl, s);
+    G->last_pulls = G->h_ctl->pulls;
     return STEINER_OK;
 }
 
@@ -635,6 +641,9 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     } else if (!strcmp(key, "dense")) {
         if (value != 0 && value != 1) return fail(STEINER_EINVAL, "dense must be 0 or 1");
         G->dense = (uint32_t)value;
+    } else if (!strcmp(key, "pull")) {
+        if (value < 0 || value > 2) return fail(STEINER_EINVAL, "pull must be 0, 1 or 2");
+        G->pull = (uint32_t)value;
     } else if (!strcmp(key, "far_scan")) {
         if (value < -1 || value > 1) return fail(STEINER_EINVAL, "far_scan must be -1, 0 or 1");
         G->far_scan = (int)value;
@@ -663,6 +672,8 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "label_bits")) return G->label_bits;
     if (!strcmp(key, "far_scan")) return G->far_scan;
     if (!strcmp(key, "dense")) return G->dense;
+    if (!strcmp(key, "pull")) return G->pull;
+    if (!strcmp(key, "pull_passes_last")) return G->last_pulls;
     if (!strcmp(key, "label_bits_last")) return G->last_label_bits;
     if (!strcmp(key, "narrow_reruns")) return (int64_t)G->narrow_reruns;
     if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);

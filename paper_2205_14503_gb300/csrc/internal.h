@@ -95,6 +95,12 @@ struct Control {
     uint32_t band_count;
     uint32_t band_hcount;
     uint32_t bands;
+    uint32_t pulls;              // heavy-arc passes run in the pull form
+    // heavy arcs of the vertices listed in the current band (a vertex
+    // listed twice counts twice), and of the vertices a pull pass found
+    // unsettled: the push and pull costs of a band's heavy-arc pass
+    unsigned long long band_hsum;
+    unsigned long long pull_hsum;
     uint32_t trace[TRACE_LEN][4];  // first iterations: near items, heavy chunks, far pile, T
     unsigned long long trace_ns[TRACE_LEN];   // their start times (global timer, ns)
     unsigned long long trace_relax[TRACE_LEN][3];   // relaxations, improvements, atomics (traced)
@@ -169,6 +175,7 @@ struct SsspParams {
     uint32_t far_scan;       // splits scan the labels instead of a far pile
     uint32_t trace;          // per-iteration relaxation counts into Control::trace_relax
     uint32_t dense;          // dense frontiers (needs far_scan and no local rounds)
+    uint32_t pull;           // heavy-arc passes: 0 push, 1 push or pull by cost, 2 pull (far_scan)
 };
 
 // SM count of the current device (queried once per device, then cached);

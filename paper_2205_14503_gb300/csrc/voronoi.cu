@@ -25,6 +25,17 @@
 // by many light paths) scans its heavy arcs once.  All of its proposals land
 // at or above T, in the far pile.  The split is on only when some arc
 // weight reaches delta.
+//
+// Pull form of the heavy-arc pass (with the far scan): once a band has
+// drained, every label below T is final, and a heavy proposal can only
+// change a vertex still at or above T.  So instead of pushing the heavy
+// arcs of the band's vertices, every unsettled vertex may read its own
+// heavy arcs and the labels at their other ends, keeping the best proposal
+// from those below T.  Both forms reach the same labels; the pass takes
+// the form that reads fewer arcs.  On a small-world graph the first band
+// holds most of the vertices and nearly all heavy arcs, while the vertices
+// left unsettled have few (direction-optimising search, Beamer et al.,
+// applied to delta-stepping's heavy-arc phase).
 #include "internal.h"
 
 namespace stn {
@@ -63,6 +74,8 @@ struct SsspArgs {
     // queues.  Ids below n_big may have HEAVY_DEG arcs or more, ids at or
     // above it have fewer (the degree order makes this a bound).
     uint32_t dense;
+    uint32_t pull;           // heavy-arc passes: 0 push, 1 by cost, 2 pull
+    uint64_t m;              // arcs (the first bound on a pull pass's cost)
     uint32_t n_big;
     uint32_t n_words;        // bitmap words, ceil(n / 32)
     uint32_t *nbm0, *nbm1;   // near bitmaps, alternating by iteration
@@ -133,6 +146,7 @@ constexpr uint32_t BAND_REGION = BAND_STAGE / SSSP_WARPS;
 constexpr int SPLIT_ILP = 4;           // 32-vertex chunks per warp step in a band split
 constexpr uint32_t DENSE_WORDS = 8;    // bitmap words per dense work item (light arcs)
 constexpr uint32_t DENSE_WORDS_HP = 8; // the same in a heavy-arc pass
+constexpr int PULL_ILP = 4;            // 32-vertex chunks per warp step in a pull pass
 
 // Where the appends of one processing segment go.
 struct PushTargets {
@@ -161,6 +175,7 @@ struct PushTargets {
     // near stamps deduplicate items only on their way to the global queue.
     bool nostamp;
     uint32_t *nostamp_stamp;     // the near stamps (for the deduplication)
+    unsigned long long *hsum;    // receives the warps' heavy-arc sums (null: none)
 };
 
 // Per-block staging buffers.  Near and band-list appends go to one region
@@ -177,6 +192,7 @@ struct Stage {
     uint32_t band_n[SSSP_WARPS];    // items staged per band region
     uint32_t dn_near[SSSP_WARPS];   // bits set in the near bitmap by each warp
     uint32_t dn_band[SSSP_WARPS];   // bits set in the band bitmap by each warp
+    uint32_t hs[SSSP_WARPS];        // heavy arcs listed (or pulled) by each warp
     uint32_t near_n[SSSP_WARPS];    // items staged per warp region
     uint32_t local_lo[SSSP_WARPS];  // region[0, local_lo) was relaxed by its warp already
     uint32_t near_off[SSSP_WARPS];  // flush: offset of each region's rest
@@ -194,6 +210,7 @@ __device__ __forceinline__ void stage_reset(Stage &st) {
         st.band_n[threadIdx.x] = 0;
         st.dn_near[threadIdx.x] = 0;
         st.dn_band[threadIdx.x] = 0;
+        st.hs[threadIdx.x] = 0;
         st.local_lo[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -226,6 +243,11 @@ __device__ __forceinline__ void flush_stage(Stage &st, const PushTargets &t, uin
         }
         if (dnn) atomicAdd(t.qn_count, dnn);
         if (dnb) atomicAdd(t.band_count, dnb);
+        if (t.hsum) {
+            unsigned long long hs = 0;
+            for (uint32_t w = 0; w < SSSP_WARPS; ++w) hs += st.hs[w];
+            if (hs) atomicAdd(t.hsum, hs);
+        }
     }
     __syncthreads();
     {   // each warp moves the rest of its own regions
@@ -437,6 +459,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
 // part is long.  A vertex without heavy arcs needs no listing.
 __device__ __forceinline__ void band_track(const SsspArgs &a, Stage &st, bool want, uint32_t u,
                                            uint32_t hdeg, uint32_t tag) {
+    uint32_t listed = 0;     // heavy arcs this lane lists
     if (a.dense) {
         // dense band list: a bit per listed vertex (the pass reads the
         // bitmap), so only the hubs need the stamp that lists them once
@@ -444,11 +467,15 @@ __device__ __forceinline__ void band_track(const SsspArgs &a, Stage &st, bool wa
         if (small) atomicOr(&a.bbm[u >> 5], 1u << (u & 31));
         const uint32_t c = (uint32_t)__popc(__ballot_sync(FULL, small));
         if (lane_id() == 0 && c) st.dn_band[threadIdx.x >> 5] += c;
+        if (small) listed = hdeg;
         want = want && hdeg >= HEAVY_DEG;
     }
     bool add = want && hdeg > 0 && atomicExch(&a.stamp_band[u], tag) != tag;
     const bool big = add && hdeg >= HEAVY_DEG;
     const uint32_t w = threadIdx.x >> 5;
+    if (add) listed = hdeg;
+    listed = __reduce_add_sync(FULL, listed);
+    if (lane_id() == 0 && listed) st.hs[w] += listed;
     region_append(add && !big, u, st.band_buf + w * BAND_REGION, &st.band_n[w], BAND_REGION, true,
                   a.band_q, &a.ctl->band_count, a.n, &a.ctl->err);
     if (big) {
@@ -464,13 +491,14 @@ __device__ __forceinline__ void band_track(const SsspArgs &a, Stage &st, bool wa
 
 // Lists high-degree vertex u (warp-uniform; deg arcs in its heavy part) in
 // the current band once, as its CHUNK-arc pieces.
-__device__ __forceinline__ void band_track_heavy(const SsspArgs &a, uint32_t u, uint32_t deg,
-                                                 uint32_t tag) {
+__device__ __forceinline__ void band_track_heavy(const SsspArgs &a, Stage &st, uint32_t u,
+                                                 uint32_t deg, uint32_t tag) {
     const uint32_t lane = lane_id();
     if (deg == 0) return;
     uint32_t add = 0;
     if (lane == 0) add = atomicExch(&a.stamp_band[u], tag) != tag;
     if (!__shfl_sync(FULL, add, 0)) return;
+    if (lane == 0) st.hs[threadIdx.x >> 5] += deg;
     const uint32_t nc = (deg + CHUNK - 1) / CHUNK;
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&a.ctl->band_hcount, nc);
@@ -547,6 +575,141 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t t) {
     return pos;
 }
 
+// Pull form of a band's heavy-arc pass (threshold T, every label below T
+// final).  Warps sweep the vertex ids 32 at a time (coalesced labels); a
+// vertex at or above T (unreached included) reads the arcs of its heavy
+// part, flattened over the warp, and the labels at their other ends; a
+// proposal (d(u) + w, rank(u)) from a settled neighbour u that beats the
+// vertex's label is sent as a fire-and-forget atomicMin (several lanes may
+// serve one vertex) and bounds far_min, as a far push proposal does.  The
+// sweep also clears the band bitmap that the push form would have read.
+// The warps' sums of the heavy arcs met go to st.hs (the pass's cost).
+template <bool NARROW>
+__device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
+                                       const uint32_t *list, uint32_t count, uint32_t *out,
+                                       uint32_t *out_count, unsigned long long &attempts,
+                                       unsigned long long &improved, bool &narrow_miss,
+                                       unsigned long long &atomics) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t met = 0;
+    uint32_t fmin = INF32;
+    // the vertices: every id, or the candidate list (then the band bitmap
+    // is cleared by a sweep of its own)
+    if (list && a.dense)
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_words;
+             i += gridDim.x * blockDim.x)
+            if (ldcg_u32(&a.bbm[i])) a.bbm[i] = 0;
+    const uint32_t nv = list ? count : a.n;
+    // PULL_ILP chunks of 32 vertices per warp step, their loads issued together
+    for (uint32_t b = warp * 32 * PULL_ILP; b < nv; b += nwarps * 32 * PULL_ILP) {
+        if (!list && a.dense && lane < PULL_ILP && (b >> 5) + lane < a.n_words &&
+            ldcg_u32(&a.bbm[(b >> 5) + lane]))
+            a.bbm[(b >> 5) + lane] = 0;
+        uint32_t vs[PULL_ILP];
+        uint64_t lab[PULL_ILP];
+        uint32_t s[PULL_ILP], r1[PULL_ILP];
+#pragma unroll
+        for (int c = 0; c < PULL_ILP; ++c) {
+            const uint32_t i = b + 32u * c + lane;
+            vs[c] = i < nv ? (list ? ldcg_u32(&list[i]) : i) : INF32;
+        }
+#pragma unroll
+        for (int c = 0; c < PULL_ILP; ++c)    // past the end: taken as settled
+            lab[c] = vs[c] != INF32 ? sssp_label<NARROW>(a, vs[c]) : 0ull;
+        bool keep[PULL_ILP];
+#pragma unroll
+        for (int c = 0; c < PULL_ILP; ++c) {
+            const uint32_t v = vs[c];
+            s[c] = r1[c] = 0;
+            keep[c] = false;
+            if (lab[c] == INF64 || (lab[c] >> 32) >= T) {          // unsettled
+                r1[c] = a.row_ptr[v + 1];
+                const uint32_t r0 = a.row_ptr[v];
+                s[c] = a.lend ? a.lend[v] : r0;
+                keep[c] = r1[c] != r0;
+            }
+        }
+        if (out) {
+            // the sweep over every id lists the unsettled vertices with arcs
+            // (the candidates of the split that follows), staged in the band
+            // regions, which a heavy-arc pass does not use
+            const uint32_t w = threadIdx.x >> 5;
+#pragma unroll
+            for (int c = 0; c < PULL_ILP; ++c)
+                region_append(keep[c], vs[c], st.band_buf + w * BAND_REGION, &st.band_n[w],
+                              BAND_REGION, true, out, out_count, a.n, &a.ctl->err);
+        }
+#pragma unroll
+        for (int c = 0; c < PULL_ILP; ++c) {
+            const uint32_t deg = r1[c] - s[c];
+            met += deg;
+            const uint32_t incl = warp_inclusive_scan(deg);
+            const uint32_t excl = incl - deg;
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            for (uint32_t j0 = 0; j0 < total; j0 += 32 * ILP) {
+                bool valid[ILP];
+                uint32_t head[ILP];
+                uint64_t hl[ILP];
+                uint2 e[ILP];
+#pragma unroll
+                for (int q = 0; q < ILP; ++q) {
+                    const uint32_t j = j0 + lane + 32 * q;
+                    valid[q] = j < total;
+                    const uint32_t owner = warp_owner_search(excl, valid[q] ? j : 0);
+                    const uint32_t so = __shfl_sync(FULL, s[c], owner);
+                    const uint32_t eo = __shfl_sync(FULL, excl, owner);
+                    hl[q] = __shfl_sync(FULL, lab[c], owner);
+                    head[q] = __shfl_sync(FULL, vs[c], owner);
+                    e[q] = make_uint2(0, 0);
+                    // the unsettled rows are read once per pass: streamed
+                    if (valid[q]) e[q] = __ldcs(&a.adj[so + (j - eo)]);
+                }
+                uint64_t tl[ILP];
+#pragma unroll
+                for (int q = 0; q < ILP; ++q) {
+                    tl[q] = INF64;
+                    if (valid[q] && e[q].y >= a.delta) tl[q] = sssp_label<NARROW>(a, e[q].x);
+                }
+#pragma unroll
+                for (int q = 0; q < ILP; ++q) {
+                    // an unsettled (or unreached) neighbour proposes nothing yet
+                    if (!valid[q] || tl[q] == INF64 || (tl[q] >> 32) >= T) continue;
+                    ++attempts;
+                    const uint64_t nd = (tl[q] >> 32) + (uint64_t)e[q].y;
+                    if (NARROW && nd > a.ldmax) {
+                        // only an unreached vertex could take it (a narrow
+                        // label's distance is at most ldmax): the host
+                        // reruns the query with 64-bit labels
+                        if (hl[q] == INF64) narrow_miss = true;
+                        continue;
+                    }
+                    if (nd >= INF32) continue;         // the scan reports the overflow
+                    const uint64_t nl64 = (nd << 32) | (tl[q] & 0xFFFFFFFFull);
+                    if (nl64 >= hl[q]) continue;
+                    if (NARROW) {
+                        atomicMin(&a.label32[head[q]],
+                                  ((uint32_t)nd << a.lshift) | (uint32_t)tl[q]);
+                    } else {
+                        atomicMin(reinterpret_cast<unsigned long long *>(&a.label[head[q]]),
+                                  (unsigned long long)nl64);
+                    }
+                    ++atomics;
+                    ++improved;
+                    fmin = min(fmin, (uint32_t)nd);
+                }
+            }
+        }
+    }
+    met = __reduce_add_sync(FULL, met);
+    fmin = __reduce_min_sync(FULL, fmin);
+    if (lane == 0) {
+        st.hs[threadIdx.x >> 5] += met;
+        if (fmin != INF32) atomicMin(&st.far_min, fmin);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the persistent near/far kernel
 // ---------------------------------------------------------------------------
@@ -560,12 +723,25 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     Control *ctl = a.ctl;
     unsigned long long attempts = 0, improved = 0;
     bool narrow_miss = false;
-    unsigned long long att0 = 0, imp0 = 0, atomics = 0, atm0 = 0;   // trace counters
-    unsigned long long t_start = 0;
+    unsigned long long atomics = 0;
+    // trace: each warp's counter sums at the start of the iteration (lane 0
+    // keeps them in shared memory, off the registers of the hot loops)
+    __shared__ unsigned long long trace_snap[SSSP_WARPS][4];
+    if (threadIdx.x < SSSP_WARPS * 4) (&trace_snap[0][0])[threadIdx.x] = 0;
     uint32_t it = 0, phase = 0, bands = 0;
     uint64_t T = a.delta;
     bool first = (blockIdx.x == 0 && threadIdx.x == 0);
     bool hp = false;               // this iteration is a band's heavy-arc pass
+    bool pull = false;             // ... in the pull form
+    // With the far scan, the first split lists every vertex left unsettled
+    // (those with arcs); later splits and pull passes visit that list,
+    // which each split shrinks, instead of every id.
+    bool listed = false;
+    // heavy arcs a pull pass would read now, bounded from above: all arcs
+    // at first, then what the last pull pass met (the unsettled set only
+    // shrinks)
+    __shared__ unsigned long long pull_bound;
+    if (threadIdx.x == 0) pull_bound = a.m;
     bool cur_dense = false;        // this iteration's light items are the bits of a near bitmap
 
     for (;;) {
@@ -581,6 +757,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         if (first) {
             ctl->near_count[(it + 2) % 3] = 0;
             ctl->heavy_count[(it + 2) % 3] = 0;
+            if (hp && pull) ++ctl->pulls;
             if (it < TRACE_LEN) {
                 ctl->trace[it][0] = n_light;
                 ctl->trace[it][1] = n_heavy;
@@ -627,6 +804,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         const uint32_t whi = (a.defer && !hp) ? a.delta : 0xFFFFFFFFu;
         const bool track = a.defer && !hp;
         const uint32_t tag_band = a.base_band + bands;
+        t.hsum = track ? &ctl->band_hsum : (hp && pull ? &ctl->pull_hsum : nullptr);
 
         // Vertices per warp batch: a thin frontier is spread over all warps
         // (fewer sequential rounds per warp), a thick one packs 32 per warp.
@@ -634,13 +812,25 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         uint32_t bsz = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : per <= 8 ? 8 : per <= 16 ? 16 : 32;
         // A dense work item is one bitmap word (32 vertices) where vertices
         // may have many arcs (ids below n_big, in the degree order the high
-        // degrees), else DENSE_WORDS words: balanced work per warp.  In a
-        // heavy-arc pass every vertex relaxes its heavier arcs: one word.
-        const uint32_t cw = hp ? DENSE_WORDS_HP : DENSE_WORDS;
+        // degrees), else DENSE_WORDS words: balanced work per warp.  A
+        // sparse bitmap (under one set bit per two words) is read 32 words
+        // per item: the sweep itself is then the cost.
+        const uint32_t cw = n_light < a.n_words / 2 ? 32u : hp ? DENSE_WORDS_HP : DENSE_WORDS;
         const uint32_t fine = min(a.n_words, (a.n_big + 1023) / 1024 * 32);
         const uint32_t n_work = n_heavy + (dense_in ? fine + (a.n_words - fine + cw - 1) / cw
                                                     : (n_light + bsz - 1) / bsz);
-        if (a.trace) t_start = global_ns();
+        if (a.trace && lane == 0) trace_snap[threadIdx.x >> 5][3] = global_ns();
+        if (hp && pull) {
+            // without a list yet, the pass sweeps every id and lists the
+            // unsettled ones as this phase's pile (empty with the far scan)
+            uint32_t *pile = fc ? a.far1 : a.far0;
+            t.bandq = pile;
+            t.band_count = &ctl->far_count[fc];
+            pull_pass<NARROW>(a, st, T, listed ? pile : nullptr,
+                              listed ? min(ldcg_u32(&ctl->far_count[fc]), a.n) : a.n,
+                              listed ? nullptr : pile, &ctl->far_count[fc], attempts, improved,
+                              narrow_miss, atomics);
+        } else
         for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
             if (wi < n_heavy) {
                 // one CHUNK of a high-degree vertex per warp
@@ -653,7 +843,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 uint32_t s = base + c * CHUNK;
                 uint32_t e = min(end, s + CHUNK);
                 uint64_t lab = sssp_label<NARROW>(a, u);
-                if (track && c == 0) band_track_heavy(a, u, a.lend ? r1 - le : r1 - r0, tag_band);
+                if (track && c == 0) band_track_heavy(a, st, u, a.lend ? r1 - le : r1 - r0, tag_band);
                 for (uint32_t b = s; b < e; b += 32 * ILP) {
                     bool valid[ILP];
                     uint32_t arc[ILP];
@@ -762,8 +952,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         if (a.trace && it < TRACE_LEN) {
             // per warp: busy time of this iteration's relaxation (sum, max)
-            const unsigned long long busy = global_ns() - t_start;
-            unsigned long long da = attempts - att0, di = improved - imp0, dm = atomics - atm0;
+            unsigned long long da = attempts, di = improved, dm = atomics;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
                 da += __shfl_xor_sync(FULL, da, o);
@@ -771,6 +960,15 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 dm += __shfl_xor_sync(FULL, dm, o);
             }
             if (lane == 0) {
+                unsigned long long *snap = trace_snap[threadIdx.x >> 5];
+                const unsigned long long busy = global_ns() - snap[3];
+                const unsigned long long sa = da, si = di, sm = dm;
+                da -= snap[0];
+                di -= snap[1];
+                dm -= snap[2];
+                snap[0] = sa;
+                snap[1] = si;
+                snap[2] = sm;
                 if (da | di) {
                     atomicAdd(&ctl->trace_relax[it][0], da);
                     atomicAdd(&ctl->trace_relax[it][1], di);
@@ -779,9 +977,6 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 atomicAdd(&ctl->trace_busy[it][0], busy);
                 atomicMax(&ctl->trace_busy[it][1], busy);
             }
-            att0 = attempts;
-            imp0 = improved;
-            atm0 = atomics;
         }
         flush_stage(st, t, a.n, &ctl->err);
         if (!grid_sync(&ctl->bar, &ctl->err)) {
@@ -794,6 +989,14 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         if (hp) {
             ++bands;               // later listings use a fresh tag
             hp = false;
+            if (pull) {
+                // every thread has read pull_bound at the decision, a
+                // barrier ago; one writes the new bound, read at the next
+                if (threadIdx.x == 0)
+                    pull_bound = ldcg_u64(reinterpret_cast<const uint64_t *>(&ctl->pull_hsum));
+                listed = true;     // the pass listed the candidates (or used the list)
+            }
+            pull = false;
         }
         if (it >= a.max_iters) {
             if (first) {
@@ -807,9 +1010,21 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         // Band drained: its heavy arcs first (one more iteration), then the
         // split.  The band lists are cleared in the split, so no block can
         // still be reading their counts here.
+        // The pull form when the band listed more heavy arcs than a pull
+        // would read: the heavy arcs of the vertices unsettled before the
+        // band less the band's own, plus the sweep over every label (taken
+        // as n / 8 arcs: coalesced, against one random label per arc).
+        // Listings count a vertex once per relaxation, which leans to the
+        // pull only when the band is large.
         if (a.defer && !was_hp &&
             (ldcg_u32(&ctl->band_count) | ldcg_u32(&ctl->band_hcount)) != 0) {
             hp = true;
+            const unsigned long long listed_hs =
+                ldcg_u64(reinterpret_cast<const uint64_t *>(&ctl->band_hsum));
+            const unsigned long long rest = pull_bound > listed_hs ? pull_bound - listed_hs : 0ull;
+            const uint32_t sweep =
+                listed ? min(ldcg_u32(&ctl->far_count[phase & 1]), a.n) : a.n;
+            pull = a.pull == 2 || (a.pull == 1 && listed_hs > rest + sweep / 8);
             continue;
         }
 
@@ -840,6 +1055,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             ctl->heavy_count[(its + 1) % 3] = 0;
             ctl->band_count = 0;
             ctl->band_hcount = 0;
+            ctl->band_hsum = 0;
         }
         stage_reset(st);
         PushTargets u;
@@ -850,18 +1066,28 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.farq = fc ? a.far0 : a.far1;
         u.far_count = &ctl->far_count[fc ^ 1];
         u.far_min = &ctl->far_min[fc ^ 1];
-        u.bandq = a.band_q;
-        u.band_count = &ctl->band_count;
+        // With the far scan the split rebuilds the pile as the candidate
+        // list: every vertex at or above T_old (the new band's frontier and
+        // all later ones; unreached vertices with arcs too), staged in the
+        // band regions, which no band listing uses during a split.
+        u.bandq = a.far_scan ? (fc ? a.far0 : a.far1) : a.band_q;
+        u.band_count = a.far_scan ? &ctl->far_count[fc ^ 1] : &ctl->band_count;
         u.tag_next = a.base_near + its;
         u.tag_far = a.base_far + phase;
         u.T = T;
         u.flush = true;
-        u.dense = a.dense;
+        // the first split sweeps every id, and sets whole bitmap words;
+        // a split over the list sets bits, and only for a list long enough
+        // that the next iteration's sweep of the bitmap pays
+        const bool from_list = a.far_scan && listed;
+        const bool dense_out = a.dense && (!from_list || nf >= a.n / 64);
+        u.dense = dense_out;
         u.nbm = (its & 1) ? a.nbm1 : a.nbm0;
         u.nostamp = false;             // the split visits each vertex once
         u.nostamp_stamp = a.stamp_near;
-        // the far pile, or with the far scan every vertex (coalesced labels)
-        const uint32_t n_split = a.far_scan ? a.n : nf;
+        u.hsum = nullptr;
+        // the far pile (or list), or with the far scan first every vertex
+        const uint32_t n_split = (a.far_scan && !from_list) ? a.n : nf;
         // SPLIT_ILP chunks of 32 per warp step, their loads issued together.
         // A vertex is met once here (the pile holds it once, the scan visits
         // each id once) and nothing relaxes during the split, so its near
@@ -869,17 +1095,18 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         for (uint32_t b = warp * 32 * SPLIT_ILP; b < n_split; b += nwarps * 32 * SPLIT_ILP) {
             uint32_t v[SPLIT_ILP], deg[SPLIT_ILP];
             uint64_t d[SPLIT_ILP];
-            bool to_near[SPLIT_ILP], cand[SPLIT_ILP], keep[SPLIT_ILP];
+            bool to_near[SPLIT_ILP], cand[SPLIT_ILP], keep[SPLIT_ILP], in[SPLIT_ILP];
 #pragma unroll
             for (int c = 0; c < SPLIT_ILP; ++c) {
                 const uint32_t i = b + 32u * c + lane;
+                in[c] = i < n_split;
                 v[c] = 0;
                 d[c] = INF32;
-                if (i < n_split) v[c] = a.far_scan ? i : ldcg_u32(&fs[i]);
+                if (in[c]) v[c] = (a.far_scan && !from_list) ? i : ldcg_u32(&fs[i]);
             }
 #pragma unroll
             for (int c = 0; c < SPLIT_ILP; ++c)
-                if (b + 32u * c + lane < n_split) d[c] = sssp_label<NARROW>(a, v[c]) >> 32;
+                if (in[c]) d[c] = sssp_label<NARROW>(a, v[c]) >> 32;
 #pragma unroll
             for (int c = 0; c < SPLIT_ILP; ++c) {
                 const bool valid = d[c] != INF32;                  // unreached or past the end
@@ -893,21 +1120,36 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                     a.stamp_near[v[c]] = u.tag_next;
                     deg[c] = r1 - r0;
                 }
-                keep[c] = cand[c] && !a.far_scan &&
-                          atomicExch(&a.stamp_far[v[c]], u.tag_far) != u.tag_far;
+                if (a.far_scan) {
+                    // the list keeps to_near and cand vertices, and unreached
+                    // ones with arcs (isolated vertices are never reached)
+                    keep[c] = to_near[c] || cand[c];
+                    if (in[c] && !valid)
+                        keep[c] = from_list || a.row_ptr[v[c] + 1] != a.row_ptr[v[c]];
+                } else {
+                    keep[c] = cand[c] &&
+                              atomicExch(&a.stamp_far[v[c]], u.tag_far) != u.tag_far;
+                }
             }
 #pragma unroll
             for (int c = 0; c < SPLIT_ILP; ++c) {
-                // dense (with the far scan a chunk is one bitmap word, empty
-                // since the band drained): light vertices as one word store
-                const bool bit = u.dense && to_near[c] && deg[c] < HEAVY_DEG;
+                // dense: light vertices as bits; from the id sweep a chunk is
+                // one bitmap word (empty since the band drained), so one store
+                const bool bit = dense_out && to_near[c] && deg[c] < HEAVY_DEG;
                 const uint32_t word = __ballot_sync(FULL, bit);
-                if (lane == 0 && word) {
+                if (from_list) {
+                    if (bit) atomicOr(&u.nbm[v[c] >> 5], 1u << (v[c] & 31));
+                } else if (lane == 0 && word) {
                     u.nbm[(b + 32u * c) >> 5] = word;
-                    st.dn_near[threadIdx.x >> 5] += (uint32_t)__popc(word);
                 }
+                if (lane == 0 && word) st.dn_near[threadIdx.x >> 5] += (uint32_t)__popc(word);
                 push_near(a, st, u, to_near[c] && !bit, v[c], deg[c]);
-                push_far(a, st, u, keep[c], cand[c], v[c], (uint32_t)d[c]);
+                if (a.far_scan) {
+                    const uint32_t w = threadIdx.x >> 5;
+                    region_append(keep[c], v[c], st.band_buf + w * BAND_REGION, &st.band_n[w],
+                                  BAND_REGION, true, u.bandq, u.band_count, a.n, &ctl->err);
+                }
+                push_far(a, st, u, keep[c] && !a.far_scan, cand[c], v[c], (uint32_t)d[c]);
             }
         }
         flush_stage(st, u, a.n, &ctl->err);
@@ -918,9 +1160,11 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         if (first) {
             ctl->far_count[fc] = 0;
             ctl->far_min[fc] = INF32;
+            ctl->pull_hsum = 0;      // read after the pass's barrier, before this one
         }
         it = its;
-        cur_dense = a.dense;          // the split set the next frontier's bits
+        cur_dense = dense_out;        // the split set the next frontier's bits
+        listed = a.far_scan != 0;
         if (it >= a.max_iters) {
             if (first) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
@@ -1047,6 +1291,8 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.far_scan = p.far_scan;
     a.trace = p.trace;
     a.dense = p.dense;
+    a.pull = p.far_scan ? p.pull : 0u;
+    a.m = g.m;
     a.n_big = g.n_big;
     a.n_words = (g.n + 31) / 32;
     a.nbm0 = ws.nbm[0];

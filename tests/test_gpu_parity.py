@@ -320,6 +320,7 @@ def _compare_forced(g, seeds, **params):
         rc, cell, dist, pred = Gd.voronoi(seeds)
         res = Gd.query_detail(seeds)
         counters = {k: Gd.get_param(k) for k in ("label_bits_last", "narrow_reruns")}
+        counters["pull_passes"] = Gd.get_param("pull_passes_last")
     assert rc == st.STEINER_OK and res.status == ref.status == oracle.OK, st.last_error()
     np.testing.assert_array_equal(cell, ref.cell)
     np.testing.assert_array_equal(dist, ref.dist)
@@ -347,7 +348,7 @@ def test_label_width_forced(bits):
         for delta in (None, 150):
             params = {"label_bits": bits} if delta is None else {"label_bits": bits, "delta": delta}
             c = _compare_forced(g, seeds, **params)
-            assert c == {"label_bits_last": bits, "narrow_reruns": 0}
+            assert (c["label_bits_last"], c["narrow_reruns"]) == (bits, 0)
 
 
 def test_narrow_labels_fall_back_to_64_bits():
@@ -363,9 +364,9 @@ def test_narrow_labels_fall_back_to_64_bits():
     g = wl.from_edges(n, np.arange(n - 1), np.arange(1, n), rng.integers(400, 512, n - 1))
     seeds = np.arange(4096, dtype=np.int32)
     c = _compare_forced(g, seeds, label_bits=32)
-    assert c == {"label_bits_last": 64, "narrow_reruns": 2}
+    assert (c["label_bits_last"], c["narrow_reruns"]) == (64, 2)
     c = _compare_forced(g, seeds)
-    assert c == {"label_bits_last": 64, "narrow_reruns": 1}
+    assert (c["label_bits_last"], c["narrow_reruns"]) == (64, 1)
 
 
 @pytest.mark.parametrize("far_scan", [0, 1])
@@ -380,6 +381,40 @@ def test_band_split_by_pile_or_scan(far_scan, delta, local):
         pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
         seeds = wl.sample_distinct(pool, k, 50 + k)
         _compare_forced(g, seeds, far_scan=far_scan, delta=delta, local_rounds=local)
+
+
+@pytest.mark.parametrize("pull", [0, 1, 2])
+@pytest.mark.parametrize("bits", [32, 64])
+def test_heavy_pass_push_or_pull(pull, bits):
+    """A band's heavy-arc pass pushes the heavy arcs of the band's vertices
+    (pull 0), reads them from the unsettled side (pull 2: every vertex at or
+    above the threshold takes the best proposal from its settled heavy-arc
+    neighbours), or picks the form that reads fewer arcs (pull 1).  All
+    three reach the oracle's labels, distance graph and tree, on skewed and
+    flat graphs, dense and sparse frontiers, many bands and few."""
+    cases = [(wl.rmat(14, 16, wmax=1000, seed=81), 400, True, 125),
+             (wl.rmat(13, 16, wmax=1000, seed=82), 7, True, 31),
+             (wl.grid(150, 110, 1000, seed=83), 60, False, 200),
+             (G.random_connected(4000, 3000, 1, 300, 84), 40, False, 60)]
+    for g, k, lcc, delta in cases:
+        pool = wl.largest_cc(g) if lcc else np.arange(g.n, dtype=np.int32)
+        seeds = wl.sample_distinct(pool, k, 80 + k)
+        for dense in (0, 1):
+            c = _compare_forced(g, seeds, pull=pull, delta=delta, dense=dense, far_scan=1,
+                                label_bits=bits)
+            if pull == 0:
+                assert c["pull_passes"] == 0
+            elif pull == 2:
+                assert c["pull_passes"] > 0
+
+
+def test_heavy_pass_pull_chosen_on_small_world_graphs():
+    """With the cost rule, the first band of an R-MAT query (most vertices
+    and nearly all heavy arcs) runs its heavy-arc pass in the pull form."""
+    g = wl.rmat(15, 16, wmax=1000, seed=85)
+    seeds = wl.sample_distinct(wl.largest_cc(g), 30, 86)
+    c = _compare_forced(g, seeds, pull=1, delta=125, far_scan=1)
+    assert c["pull_passes"] >= 1
 
 
 @pytest.mark.parametrize("wmax", [10_000, 100_000])
