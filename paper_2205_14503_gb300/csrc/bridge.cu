@@ -76,7 +76,8 @@ __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t
         }
         uint64_t key = (b << 32) | (uint32_t)(cbase + arc);
         uint64_t *slot = &a.pairtab[pair_slot(cv, cu, a.k)];
-        if (key < ldcg_u64(slot))
+        // a cached read may be stale, i.e. larger: at worst one atomic more
+        if (key < __ldg(reinterpret_cast<const unsigned long long *>(slot)))
             atomicMin(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)key);
     }
 }
