@@ -363,14 +363,15 @@ def run_ours(args, world, rank, local):
     if args.tuned:
         # explicit (delta, blocks, local rounds), e.g. for profiling captures
         vals = [int(x) for x in args.tuned.split(",")]
-        d, b, lr, lb, fs = vals + [0, 0, 0, 0, -1][len(vals):]
+        d, b, lr, lb, fs, tl = vals + [0, 0, 0, 0, -1, 1][len(vals):]
         G.set_param("delta", d)
         G.set_param("sssp_blocks", b)
         G.set_param("local_rounds", lr)
         G.set_param("label_bits", lb)
         G.set_param("far_scan", fs)
+        G.set_param("tail", tl)
         tuned = {"delta": d, "sssp_blocks": G.get_param("sssp_blocks"), "local_rounds": lr,
-                 "label_bits": lb, "far_scan": fs}
+                 "label_bits": lb, "far_scan": fs, "tail": tl}
     elif not args.no_autotune:
         # set-up, untimed: band width, grid size, label width and split mode
         # for this graph, tuned on the held-out seed set
@@ -414,6 +415,8 @@ def run_ours(args, world, rank, local):
     barrier(world)
     label_bits = G.get_param("label_bits_last")      # the width the timed queries used
     narrow_reruns = G.get_param("narrow_reruns")
+    pull_passes = G.get_param("pull_passes_last")
+    tail_iteration = G.get_param("tail_iteration_last")
     G.close()
 
     if rank != 0:
@@ -459,6 +462,8 @@ def run_ours(args, world, rank, local):
                  "local_rounds": tuned["local_rounds"] if tuned else None,
                  "label_bits": label_bits, "narrow_reruns": narrow_reruns,
                  "far_scan": tuned.get("far_scan") if tuned else None,
+                 "tail": tuned.get("tail") if tuned else None,
+                 "pull_passes": pull_passes, "tail_iteration": tail_iteration,
                  "autotuned": bool(tuned) and not args.tuned},
         "tree": {"edges": int(res.edges.shape[0]), "total": int(res.total)},
         "graph_load_s": load_s,
@@ -785,8 +790,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default band width and grid size")
     ap.add_argument("--tuned", default=None,
-                    help="DELTA,BLOCKS,LOCAL_ROUNDS[,LABEL_BITS,FAR_SCAN] instead of autotuning "
-                         "(BLOCKS 0 = all; LABEL_BITS 0/32/64; FAR_SCAN -1/0/1)")
+                    help="DELTA,BLOCKS,LOCAL_ROUNDS[,LABEL_BITS,FAR_SCAN,TAIL] instead of "
+                         "autotuning (BLOCKS 0 = all; LABEL_BITS 0/32/64; FAR_SCAN -1/0/1; "
+                         "TAIL 0/1)")
     ap.add_argument("--side", type=int, default=None,
                     help="profiling only: a side x side grid instead of the workload")
     ap.add_argument("--k", type=int, default=None,

@@ -229,6 +229,9 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  2 pulls: every vertex still at or above the threshold
  *                  reads its own heavy arcs and takes the best proposal
  *                  from the settled vertices at their other ends
+ *   "tail"         1 (default): after a heavy-arc pass in the pull form the
+ *                  rest of the Voronoi phase runs as one unbounded band (a
+ *                  frontier Bellman-Ford over whole rows); 0 keeps the bands
  *   "label_bits"   width of the Voronoi labels: 0 (default) chooses per
  *                  query, 32 or 64 force it.  A 32-bit label holds
  *                  (distance << b) | rank with b the bits of the largest
@@ -237,7 +240,9 @@ int steiner_serve_stop(steiner_graph_t g);
  * steiner_get_param also reads "sssp_max_blocks", "sm_count",
  * "heavy_chunks", "label_bits_last" (the width the last query ended with),
  * "narrow_reruns" (queries rerun with 64-bit labels), "pull_passes_last"
- * (heavy-arc passes of the last query run in the pull form) and the multi-query
+ * (heavy-arc passes of the last query run in the pull form),
+ * "tail_iteration_last" (the iteration its unbounded tail began at, 0 for
+ * none) and the multi-query
  * engine's tracing counters
  * ("batch_ms_sssp", "batch_ms_scan", "batch_ms_tail", "batch_ms_admit" in
  * microseconds, "batch_launches", "batch_iterations", "batch_items",

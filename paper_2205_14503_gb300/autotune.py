@@ -76,6 +76,7 @@ def apply_cached(G: "st.SteinerGraph", graph, cache_path: str = DEFAULT_CACHE,
     G.set_param("local_rounds", entry.get("local_rounds", 0))
     G.set_param("label_bits", entry.get("label_bits", 0))
     G.set_param("far_scan", entry.get("far_scan", -1))
+    G.set_param("tail", entry.get("tail", 1))
     return entry
 
 
@@ -96,15 +97,18 @@ def tune(G: "st.SteinerGraph", graph, sample_seeds,
          local_rounds=(0, 32), label_bits=(0, 64), far_scan=(0, 1), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
     """Times whole queries over a grid of (delta, blocks, local rounds) on
-    the sample seed sets (label width and split mode automatic), then over
-    (label width, split mode) at the best point; applies the fastest and
-    (optionally) caches it."""
+    the sample seed sets (label width and split mode automatic), then two
+    band widths between the grid's points next to the best one, then
+    (label width, split mode) at the best point, then the banded rest
+    against the unbounded tail; applies the fastest and (optionally) caches
+    it."""
     d0 = G.get_param("delta")
     bmax = G.get_param("sssp_max_blocks")
     sm = max(1, G.get_param("sm_count"))
     trials = []
     G.set_param("label_bits", 0)
     G.set_param("far_scan", -1)
+    G.set_param("tail", 1)
     for fb in block_fractions:
         blocks = max(sm, int(round(bmax * fb / sm)) * sm)
         blocks = min(blocks, bmax)
@@ -115,6 +119,16 @@ def tune(G: "st.SteinerGraph", graph, sample_seeds,
                 G.set_param("sssp_blocks", blocks)
                 G.set_param("local_rounds", lr)
                 trials.append((_time(G, sample_seeds, reps), delta, blocks, lr, 0, -1))
+    trials.sort()
+    _, delta, blocks, lr, _, _ = trials[0]
+    G.set_param("sssp_blocks", blocks)
+    G.set_param("local_rounds", lr)
+    # refine the band width between the grid's powers of two
+    for fr in (0.707, 1.414):
+        d = max(1, int(round(delta * fr)))
+        if all(d != t[1] for t in trials):
+            G.set_param("delta", d)
+            trials.append((_time(G, sample_seeds, reps), d, blocks, lr, 0, -1))
     trials.sort()
     _, delta, blocks, lr, _, _ = trials[0]
     G.set_param("delta", delta)
@@ -132,8 +146,16 @@ def tune(G: "st.SteinerGraph", graph, sample_seeds,
     G.set_param("local_rounds", lr)
     G.set_param("label_bits", lb)
     G.set_param("far_scan", fs)
+    # every trial so far ran with the unbounded tail after a pull pass; the
+    # banded rest at the chosen point
+    G.set_param("tail", 0)
+    no_tail_ms = _time(G, sample_seeds, reps)
+    tail = 0 if no_tail_ms < best_ms else 1
+    best_ms = min(best_ms, no_tail_ms)
+    G.set_param("tail", tail)
     entry = {"delta": delta, "sssp_blocks": blocks, "local_rounds": lr, "label_bits": lb,
-             "far_scan": fs, "ms_query": best_ms, "default_delta": d0, "max_blocks": bmax,
+             "far_scan": fs, "tail": tail, "ms_no_tail": no_tail_ms, "ms_query": best_ms,
+             "default_delta": d0, "max_blocks": bmax,
              "trials": [{"ms": t, "delta": d, "blocks": b, "local_rounds": r, "label_bits": x,
                          "far_scan": y} for t, d, b, r, x, y in trials]}
     if cache_path:

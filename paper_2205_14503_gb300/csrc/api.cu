@@ -86,6 +86,10 @@ struct steiner_graph {
     // 0 always pushes, 2 always pulls.
     uint32_t pull = 1;
     uint32_t last_pulls = 0;
+    // After a heavy-arc pass in the pull form, the rest of the Voronoi phase
+    // runs as one unbounded band (1, default) or keeps its bands (0).
+    uint32_t tail = 1;
+    uint32_t last_tail_it = 0;
     uint32_t narrow_fail_dbits = 0;   // most distance bits a narrow attempt ran out of
     uint32_t last_label_bits = 0;
     uint64_t narrow_reruns = 0;
@@ -248,7 +252,8 @@ int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool ful
     static const bool trace = getenv("STEINER_TRACE") != nullptr;
     const uint32_t dense = (G->dense && far_scan && G->local_rounds == 0) ? 1u : 0u;
     SsspParams p{G->delta, G->max_iters, ws.epoch_near, ws.epoch_far, G->local_rounds,
-                 ws.epoch_band, far_scan, trace ? 1u : 0u, dense, far_scan ? G->pull : 0u};
+                 ws.epoch_band, far_scan, trace ? 1u : 0u, dense, far_scan ? G->pull : 0u,
+                 G->tail};
     CK(cudaEventRecord(G->ev[0], s));
     CK(ensure_partition(G, G->delta));
     CK(launch_init(G->g, ws, k, G->delta, s));
@@ -277,6 +282,7 @@ int run_pipeline_once(steiner_graph *G, const std::vector<int32_t> &ss, bool ful
     }
     advance_epochs(ws, *G->h_ctl, s);
     G->last_pulls = G->h_ctl->pulls;
+    G->last_tail_it = G->h_ctl->tail_it;
     return STEINER_OK;
 }
 
@@ -641,6 +647,9 @@ int steiner_set_param(steiner_graph_t G, const char *key, int64_t value) {
     } else if (!strcmp(key, "dense")) {
         if (value != 0 && value != 1) return fail(STEINER_EINVAL, "dense must be 0 or 1");
         G->dense = (uint32_t)value;
+    } else if (!strcmp(key, "tail")) {
+        if (value != 0 && value != 1) return fail(STEINER_EINVAL, "tail must be 0 or 1");
+        G->tail = (uint32_t)value;
     } else if (!strcmp(key, "pull")) {
         if (value < 0 || value > 2) return fail(STEINER_EINVAL, "pull must be 0, 1 or 2");
         G->pull = (uint32_t)value;
@@ -674,6 +683,8 @@ int64_t steiner_get_param(steiner_graph_t G, const char *key) {
     if (!strcmp(key, "dense")) return G->dense;
     if (!strcmp(key, "pull")) return G->pull;
     if (!strcmp(key, "pull_passes_last")) return G->last_pulls;
+    if (!strcmp(key, "tail")) return G->tail;
+    if (!strcmp(key, "tail_iteration_last")) return G->last_tail_it;
     if (!strcmp(key, "label_bits_last")) return G->last_label_bits;
     if (!strcmp(key, "narrow_reruns")) return (int64_t)G->narrow_reruns;
     if (!strncmp(key, "batch_", 6)) return batch_counter(G->batch, key);

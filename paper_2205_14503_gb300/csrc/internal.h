@@ -96,6 +96,7 @@ struct Control {
     uint32_t band_hcount;
     uint32_t bands;
     uint32_t pulls;              // heavy-arc passes run in the pull form
+    uint32_t tail_it;            // iteration the unbounded tail band began at (0: none)
     // heavy arcs of the vertices listed in the current band (a vertex
     // listed twice counts twice), and of the vertices a pull pass found
     // unsettled: the push and pull costs of a band's heavy-arc pass
@@ -176,6 +177,7 @@ struct SsspParams {
     uint32_t trace;          // per-iteration relaxation counts into Control::trace_relax
     uint32_t dense;          // dense frontiers (needs far_scan and no local rounds)
     uint32_t pull;           // heavy-arc passes: 0 push, 1 push or pull by cost, 2 pull (far_scan)
+    uint32_t tail;           // after a pull pass, the rest as one unbounded band (1) or not (0)
 };
 
 // SM count of the current device (queried once per device, then cached);

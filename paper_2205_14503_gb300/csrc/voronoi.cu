@@ -75,6 +75,7 @@ struct SsspArgs {
     // above it have fewer (the degree order makes this a bound).
     uint32_t dense;
     uint32_t pull;           // heavy-arc passes: 0 push, 1 by cost, 2 pull
+    uint32_t tail;           // 1: after a pull pass the rest runs as one unbounded band
     uint64_t m;              // arcs (the first bound on a pull pass's cost)
     uint32_t n_big;
     uint32_t n_words;        // bitmap words, ceil(n / 32)
@@ -176,6 +177,9 @@ struct PushTargets {
     bool nostamp;
     uint32_t *nostamp_stamp;     // the near stamps (for the deduplication)
     unsigned long long *hsum;    // receives the warps' heavy-arc sums (null: none)
+    // end of each row's part relaxed by a near vertex (the light part while
+    // the light/heavy split is on); null: whole rows
+    const uint32_t *lend;
 };
 
 // Per-block staging buffers.  Near and band-list appends go to one region
@@ -414,7 +418,7 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
             // reads its degree first and, if it is one, joins the chunk queue
             if (v < a.n_big) {
                 const uint32_t r0 = a.row_ptr[v];
-                deg[u] = (a.lend ? a.lend[v] : a.row_ptr[v + 1]) - r0;
+                deg[u] = (t.lend ? t.lend[v] : a.row_ptr[v + 1]) - r0;
             }
             if (deg[u] >= HEAVY_DEG) {
                 to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
@@ -426,13 +430,13 @@ __device__ __forceinline__ void relax_group(const SsspArgs &a, Stage &st, const 
             // ids at or above n_big cannot be hubs: no look at the row
             if (v < a.n_big) {
                 const uint32_t r0 = a.row_ptr[v];
-                deg[u] = (a.lend ? a.lend[v] : a.row_ptr[v + 1]) - r0;
+                deg[u] = (t.lend ? t.lend[v] : a.row_ptr[v + 1]) - r0;
             }
             to_near[u] = deg[u] < HEAVY_DEG ||     // hubs join the chunk queue once
                          atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
         } else if (nd[u] < t.T) {
             uint32_t r0 = a.row_ptr[v];                           // independent of the exchange
-            uint32_t r1 = a.lend ? a.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
+            uint32_t r1 = t.lend ? t.lend[v] : a.row_ptr[v + 1];  // end of the part relaxed near
             to_near[u] = atomicExch(&a.stamp_near[v], t.tag_next) != t.tag_next;
             deg[u] = r1 - r0;
         } else {
@@ -525,14 +529,14 @@ __device__ __forceinline__ void relax_vertices(const SsspArgs &a, Stage &st, con
     uint64_t lab = INF64;
     if (has) {
         const uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
-        const uint32_t le = a.lend ? a.lend[u] : r1;
+        const uint32_t le = t.lend ? t.lend[u] : r1;
         if (hp) {                       // the heavy part (or the whole row)
-            s = a.lend ? le : r0;
+            s = t.lend ? le : r0;
             deg = r1 - s;
         } else {                        // the light part
             s = r0;
             deg = le - r0;
-            hdeg = a.lend ? r1 - le : r1 - r0;
+            hdeg = t.lend ? r1 - le : r1 - r0;
         }
         lab = sssp_label<NARROW>(a, u);
         if (lab == INF64) deg = 0;
@@ -737,6 +741,13 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     // (those with arcs); later splits and pull passes visit that list,
     // which each split shrinks, instead of every id.
     bool listed = false;
+    // Tail: after a band whose heavy-arc pass ran in the pull form (it
+    // settled most of the graph's heavy arcs), the rest runs as one
+    // unbounded band, a frontier Bellman-Ford over whole rows: on a
+    // small-world graph the unsettled vertices hang off the settled core
+    // by short chains, and a few iterations reach the fixed point that a
+    // band per delta would approach in many splits.
+    bool tail = false, tail_next = false;
     // heavy arcs a pull pass would read now, bounded from above: all arcs
     // at first, then what the last pull pass met (the unsettled set only
     // shrinks)
@@ -800,9 +811,11 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         t.nostamp_stamp = a.stamp_near;
         // arcs relaxed by this iteration: all; light ones while a band
         // iterates under the split; heavy ones in the band's closing pass
+        // (in the tail every relaxation covers whole rows)
         const uint32_t wlo = hp ? a.delta : 0u;
-        const uint32_t whi = (a.defer && !hp) ? a.delta : 0xFFFFFFFFu;
-        const bool track = a.defer && !hp;
+        const uint32_t whi = (a.defer && !hp && !tail) ? a.delta : 0xFFFFFFFFu;
+        const bool track = a.defer && !hp && !tail;
+        t.lend = tail ? nullptr : a.lend;
         const uint32_t tag_band = a.base_band + bands;
         t.hsum = track ? &ctl->band_hsum : (hp && pull ? &ctl->pull_hsum : nullptr);
 
@@ -837,13 +850,13 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 uint64_t item = __ldcg(reinterpret_cast<const unsigned long long *>(&hqc[wi]));
                 uint32_t u = (uint32_t)(item >> 32), c = (uint32_t)item;
                 uint32_t r0 = a.row_ptr[u], r1 = a.row_ptr[u + 1];
-                const uint32_t le = a.lend ? a.lend[u] : r1;      // light part [r0, le)
+                const uint32_t le = t.lend ? t.lend[u] : r1;      // light part [r0, le)
                 // a band's heavy pass covers the heavy part, else the light one
-                const uint32_t base = hp && a.lend ? le : r0, end = hp ? r1 : le;
+                const uint32_t base = hp && t.lend ? le : r0, end = hp ? r1 : le;
                 uint32_t s = base + c * CHUNK;
                 uint32_t e = min(end, s + CHUNK);
                 uint64_t lab = sssp_label<NARROW>(a, u);
-                if (track && c == 0) band_track_heavy(a, st, u, a.lend ? r1 - le : r1 - r0, tag_band);
+                if (track && c == 0) band_track_heavy(a, st, u, t.lend ? r1 - le : r1 - r0, tag_band);
                 for (uint32_t b = s; b < e; b += 32 * ILP) {
                     bool valid[ILP];
                     uint32_t arc[ILP];
@@ -919,9 +932,9 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                         // all a round needs
                         s = a.row_ptr[u];
                         const uint32_t r1 = a.row_ptr[u + 1];
-                        const uint32_t le = a.lend ? a.lend[u] : r1;
+                        const uint32_t le = t.lend ? t.lend[u] : r1;
                         deg = le - s;
-                        hdeg = a.lend ? r1 - le : r1 - s;
+                        hdeg = t.lend ? r1 - le : r1 - s;
                         lab = sssp_label<NARROW>(a, u);
                     }
                     if (track) band_track(a, st, has, u, hdeg, tag_band);
@@ -990,6 +1003,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             ++bands;               // later listings use a fresh tag
             hp = false;
             if (pull) {
+                tail_next = a.tail != 0;
                 // every thread has read pull_bound at the decision, a
                 // barrier ago; one writes the new bound, read at the next
                 if (threadIdx.x == 0)
@@ -1016,7 +1030,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         // as n / 8 arcs: coalesced, against one random label per arc).
         // Listings count a vertex once per relaxation, which leans to the
         // pull only when the band is large.
-        if (a.defer && !was_hp &&
+        if (a.defer && !was_hp && !tail &&
             (ldcg_u32(&ctl->band_count) | ldcg_u32(&ctl->band_hcount)) != 0) {
             hp = true;
             const unsigned long long listed_hs =
@@ -1047,6 +1061,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         uint64_t T_old = T;
         T = (fmin != INF32 && (uint64_t)fmin > T ? (uint64_t)fmin : T) + a.delta;
+        if (tail_next) {
+            T = INF32;                 // every reached distance is below it
+            tail = true;
+            tail_next = false;
+            if (first) ctl->tail_it = it + 1;
+        }
         ++phase;
         const uint32_t *fs = fc ? a.far1 : a.far0;
         const uint32_t its = it + 1;
@@ -1086,6 +1106,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         u.nostamp = false;             // the split visits each vertex once
         u.nostamp_stamp = a.stamp_near;
         u.hsum = nullptr;
+        u.lend = tail ? nullptr : a.lend;
         // the far pile (or list), or with the far scan first every vertex
         const uint32_t n_split = (a.far_scan && !from_list) ? a.n : nf;
         // SPLIT_ILP chunks of 32 per warp step, their loads issued together.
@@ -1116,7 +1137,7 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
                 // dense: ids at or above n_big are light without a look at the row
                 if (to_near[c] && (!a.dense || v[c] < a.n_big)) {
                     const uint32_t r0 = a.row_ptr[v[c]];
-                    const uint32_t r1 = a.lend ? a.lend[v[c]] : a.row_ptr[v[c] + 1];
+                    const uint32_t r1 = u.lend ? u.lend[v[c]] : a.row_ptr[v[c] + 1];
                     a.stamp_near[v[c]] = u.tag_next;
                     deg[c] = r1 - r0;
                 }
@@ -1292,6 +1313,7 @@ cudaError_t launch_sssp(const DevGraph &g, Workspace &ws, const Geometry &geo,
     a.trace = p.trace;
     a.dense = p.dense;
     a.pull = p.far_scan ? p.pull : 0u;
+    a.tail = p.tail;
     a.m = g.m;
     a.n_big = g.n_big;
     a.n_words = (g.n + 31) / 32;

@@ -321,6 +321,7 @@ def _compare_forced(g, seeds, **params):
         res = Gd.query_detail(seeds)
         counters = {k: Gd.get_param(k) for k in ("label_bits_last", "narrow_reruns")}
         counters["pull_passes"] = Gd.get_param("pull_passes_last")
+        counters["tail_iteration"] = Gd.get_param("tail_iteration_last")
     assert rc == st.STEINER_OK and res.status == ref.status == oracle.OK, st.last_error()
     np.testing.assert_array_equal(cell, ref.cell)
     np.testing.assert_array_equal(dist, ref.dist)
@@ -383,15 +384,18 @@ def test_band_split_by_pile_or_scan(far_scan, delta, local):
         _compare_forced(g, seeds, far_scan=far_scan, delta=delta, local_rounds=local)
 
 
+@pytest.mark.parametrize("tail", [0, 1])
 @pytest.mark.parametrize("pull", [0, 1, 2])
 @pytest.mark.parametrize("bits", [32, 64])
-def test_heavy_pass_push_or_pull(pull, bits):
+def test_heavy_pass_push_or_pull(pull, bits, tail):
     """A band's heavy-arc pass pushes the heavy arcs of the band's vertices
     (pull 0), reads them from the unsettled side (pull 2: every vertex at or
     above the threshold takes the best proposal from its settled heavy-arc
-    neighbours), or picks the form that reads fewer arcs (pull 1).  All
-    three reach the oracle's labels, distance graph and tree, on skewed and
-    flat graphs, dense and sparse frontiers, many bands and few."""
+    neighbours), or picks the form that reads fewer arcs (pull 1); after a
+    pull pass the rest runs as one unbounded band over whole rows (tail 1)
+    or keeps its bands (tail 0).  All reach the oracle's labels, distance
+    graph and tree, on skewed and flat graphs, dense and sparse frontiers,
+    many bands and few."""
     cases = [(wl.rmat(14, 16, wmax=1000, seed=81), 400, True, 125),
              (wl.rmat(13, 16, wmax=1000, seed=82), 7, True, 31),
              (wl.grid(150, 110, 1000, seed=83), 60, False, 200),
@@ -401,11 +405,16 @@ def test_heavy_pass_push_or_pull(pull, bits):
         seeds = wl.sample_distinct(pool, k, 80 + k)
         for dense in (0, 1):
             c = _compare_forced(g, seeds, pull=pull, delta=delta, dense=dense, far_scan=1,
-                                label_bits=bits)
+                                label_bits=bits, tail=tail)
             if pull == 0:
-                assert c["pull_passes"] == 0
+                assert c["pull_passes"] == 0 and c["tail_iteration"] == 0
             elif pull == 2:
                 assert c["pull_passes"] > 0
+            if tail == 0:
+                assert c["tail_iteration"] == 0
+            elif pull == 2:
+                # the first pull pass starts the tail, unless it converged
+                assert c["pull_passes"] == 1
 
 
 def test_heavy_pass_pull_chosen_on_small_world_graphs():
@@ -414,7 +423,7 @@ def test_heavy_pass_pull_chosen_on_small_world_graphs():
     g = wl.rmat(15, 16, wmax=1000, seed=85)
     seeds = wl.sample_distinct(wl.largest_cc(g), 30, 86)
     c = _compare_forced(g, seeds, pull=1, delta=125, far_scan=1)
-    assert c["pull_passes"] >= 1
+    assert c["pull_passes"] == 1 and c["tail_iteration"] > 0
 
 
 @pytest.mark.parametrize("wmax", [10_000, 100_000])
