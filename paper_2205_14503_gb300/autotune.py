@@ -93,7 +93,7 @@ def _time(G, sample_seeds, reps):
 
 
 def tune(G: "st.SteinerGraph", graph, sample_seeds,
-         delta_factors=(0.0625, 0.125, 0.25, 0.5, 1, 2), block_fractions=(0.5, 1.0),
+         delta_factors=(1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2, 1, 2), block_fractions=(0.5, 1.0),
          local_rounds=(0, 32), label_bits=(0, 64), far_scan=(0, 1), reps: int = 2,
          cache_path: str | None = DEFAULT_CACHE, device: int = 0) -> dict:
     """Times whole queries over a grid of (delta, blocks, local rounds) on

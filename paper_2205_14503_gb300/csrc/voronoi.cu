@@ -580,23 +580,48 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t t) {
 }
 
 // Pull form of a band's heavy-arc pass (threshold T, every label below T
-// final).  Warps sweep the vertex ids 32 at a time (coalesced labels); a
-// vertex at or above T (unreached included) reads the arcs of its heavy
-// part, flattened over the warp, and the labels at their other ends; a
-// proposal (d(u) + w, rank(u)) from a settled neighbour u that beats the
-// vertex's label is sent as a fire-and-forget atomicMin (several lanes may
-// serve one vertex) and bounds far_min, as a far push proposal does.  The
-// sweep also clears the band bitmap that the push form would have read.
-// The warps' sums of the heavy arcs met go to st.hs (the pass's cost).
+// final).  Warps sweep the vertex ids 32 at a time (coalesced labels), or
+// the candidate list; a vertex at or above T (unreached included) reads
+// the arcs of its heavy part, flattened over the warp, and the labels at
+// their other ends.  The best proposal (d(u) + w, rank(u)) from a settled
+// neighbour u is gathered per vertex in shared memory (pmin: one slot per
+// vertex of the warp's step) and, if it beats the vertex's label, sent as
+// one fire-and-forget atomicMin; it bounds far_min as a far push proposal
+// does.  The sweep also clears the band bitmap that the push form would
+// have read.  The warps' sums of the heavy arcs met go to st.hs (the pass's
+// cost).
+// `out` (sweep of every id, no tail): the unsettled vertices with arcs are
+// listed there, the candidates of the split that follows.
+// `tail`: the pass starts the unbounded tail band: every unsettled vertex
+// whose label is now finite joins the next frontier (t), with its whole row.
 template <bool NARROW>
-__device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
+__device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st,
+                                       unsigned long long (*pmin)[32 * PULL_ILP], uint64_t T,
                                        const uint32_t *list, uint32_t count, uint32_t *out,
-                                       uint32_t *out_count, unsigned long long &attempts,
+                                       uint32_t *out_count, bool tail, uint32_t *nbm,
+                                       uint32_t *qn, uint32_t *qn_count, uint64_t *hqn,
+                                       uint32_t *hqn_count, unsigned long long &attempts,
                                        unsigned long long &improved, bool &narrow_miss,
                                        unsigned long long &atomics) {
     const uint32_t lane = lane_id();
+    const uint32_t wib = threadIdx.x >> 5;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long *pm = pmin[wib];
+    // where the tail's first frontier goes (light vertices as bits when dense)
+    PushTargets t;
+    t.qn = qn;
+    t.qn_count = qn_count;
+    t.hqn = hqn;
+    t.hqn_count = hqn_count;
+    t.flush = true;
+    t.dense = a.dense != 0;
+    t.nbm = nbm;
+    t.nostamp = false;
+    t.nostamp_stamp = nullptr;
+    t.tag_next = 0;
+    t.hsum = nullptr;
+    t.lend = nullptr;
     uint32_t met = 0;
     uint32_t fmin = INF32;
     // the vertices: every id, or the candidate list (then the band bitmap
@@ -613,38 +638,39 @@ __device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
             a.bbm[(b >> 5) + lane] = 0;
         uint32_t vs[PULL_ILP];
         uint64_t lab[PULL_ILP];
-        uint32_t s[PULL_ILP], r1[PULL_ILP];
+        uint32_t s[PULL_ILP], r1[PULL_ILP], r0[PULL_ILP];
 #pragma unroll
         for (int c = 0; c < PULL_ILP; ++c) {
             const uint32_t i = b + 32u * c + lane;
             vs[c] = i < nv ? (list ? ldcg_u32(&list[i]) : i) : INF32;
+            pm[32 * c + lane] = INF64;
         }
 #pragma unroll
         for (int c = 0; c < PULL_ILP; ++c)    // past the end: taken as settled
             lab[c] = vs[c] != INF32 ? sssp_label<NARROW>(a, vs[c]) : 0ull;
-        bool keep[PULL_ILP];
+        bool uns[PULL_ILP];
 #pragma unroll
         for (int c = 0; c < PULL_ILP; ++c) {
             const uint32_t v = vs[c];
-            s[c] = r1[c] = 0;
-            keep[c] = false;
-            if (lab[c] == INF64 || (lab[c] >> 32) >= T) {          // unsettled
+            s[c] = r1[c] = r0[c] = 0;
+            uns[c] = lab[c] == INF64 || (lab[c] >> 32) >= T;
+            if (uns[c]) {
                 r1[c] = a.row_ptr[v + 1];
-                const uint32_t r0 = a.row_ptr[v];
-                s[c] = a.lend ? a.lend[v] : r0;
-                keep[c] = r1[c] != r0;
+                r0[c] = a.row_ptr[v];
+                s[c] = a.lend ? a.lend[v] : r0[c];
             }
         }
         if (out) {
             // the sweep over every id lists the unsettled vertices with arcs
             // (the candidates of the split that follows), staged in the band
             // regions, which a heavy-arc pass does not use
-            const uint32_t w = threadIdx.x >> 5;
 #pragma unroll
             for (int c = 0; c < PULL_ILP; ++c)
-                region_append(keep[c], vs[c], st.band_buf + w * BAND_REGION, &st.band_n[w],
-                              BAND_REGION, true, out, out_count, a.n, &a.ctl->err);
+                region_append(uns[c] && r1[c] != r0[c], vs[c], st.band_buf + wib * BAND_REGION,
+                              &st.band_n[wib], BAND_REGION, true, out, out_count, a.n,
+                              &a.ctl->err);
         }
+        __syncwarp();
 #pragma unroll
         for (int c = 0; c < PULL_ILP; ++c) {
             const uint32_t deg = r1[c] - s[c];
@@ -654,7 +680,7 @@ __device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
             const uint32_t total = __shfl_sync(FULL, incl, 31);
             for (uint32_t j0 = 0; j0 < total; j0 += 32 * ILP) {
                 bool valid[ILP];
-                uint32_t head[ILP];
+                uint32_t slot[ILP];
                 uint64_t hl[ILP];
                 uint2 e[ILP];
 #pragma unroll
@@ -665,7 +691,7 @@ __device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
                     const uint32_t so = __shfl_sync(FULL, s[c], owner);
                     const uint32_t eo = __shfl_sync(FULL, excl, owner);
                     hl[q] = __shfl_sync(FULL, lab[c], owner);
-                    head[q] = __shfl_sync(FULL, vs[c], owner);
+                    slot[q] = 32u * c + owner;
                     e[q] = make_uint2(0, 0);
                     // the unsettled rows are read once per pass: streamed
                     if (valid[q]) e[q] = __ldcs(&a.adj[so + (j - eo)]);
@@ -691,25 +717,49 @@ __device__ __noinline__ void pull_pass(const SsspArgs &a, Stage &st, uint64_t T,
                     }
                     if (nd >= INF32) continue;         // the scan reports the overflow
                     const uint64_t nl64 = (nd << 32) | (tl[q] & 0xFFFFFFFFull);
-                    if (nl64 >= hl[q]) continue;
-                    if (NARROW) {
-                        atomicMin(&a.label32[head[q]],
-                                  ((uint32_t)nd << a.lshift) | (uint32_t)tl[q]);
-                    } else {
-                        atomicMin(reinterpret_cast<unsigned long long *>(&a.label[head[q]]),
-                                  (unsigned long long)nl64);
-                    }
-                    ++atomics;
-                    ++improved;
-                    fmin = min(fmin, (uint32_t)nd);
+                    if (nl64 < hl[q]) atomicMin(&pm[slot[q]], (unsigned long long)nl64);
                 }
             }
         }
+        __syncwarp();
+        // each lane settles its own vertices: one atomic per improved one
+#pragma unroll
+        for (int c = 0; c < PULL_ILP; ++c) {
+            const uint64_t best = pm[32 * c + lane];
+            uint64_t now = lab[c];
+            if (uns[c] && best < lab[c]) {
+                if (NARROW)
+                    atomicMin(&a.label32[vs[c]],
+                              ((uint32_t)(best >> 32) << a.lshift) | (uint32_t)best);
+                else
+                    atomicMin(reinterpret_cast<unsigned long long *>(&a.label[vs[c]]),
+                              (unsigned long long)best);
+                ++atomics;
+                ++improved;
+                fmin = min(fmin, (uint32_t)(best >> 32));
+                now = best;
+            }
+            if (tail) {
+                // reached and unsettled: the tail's first frontier, whole rows
+                const bool want = uns[c] && now != INF64 && r1[c] != r0[c];
+                const uint32_t deg = r1[c] - r0[c];
+                const bool bit = t.dense && want && deg < HEAVY_DEG;
+                const uint32_t word = __ballot_sync(FULL, bit);
+                if (!list) {
+                    if (lane == 0 && word) t.nbm[(b + 32u * c) >> 5] = word;
+                } else if (bit) {
+                    atomicOr(&t.nbm[vs[c] >> 5], 1u << (vs[c] & 31));
+                }
+                if (lane == 0 && word) st.dn_near[wib] += (uint32_t)__popc(word);
+                push_near(a, st, t, want && !bit, vs[c], deg);
+            }
+        }
+        __syncwarp();
     }
     met = __reduce_add_sync(FULL, met);
     fmin = __reduce_min_sync(FULL, fmin);
     if (lane == 0) {
-        st.hs[threadIdx.x >> 5] += met;
+        st.hs[wib] += met;
         if (fmin != INF32) atomicMin(&st.far_min, fmin);
     }
 }
@@ -747,7 +797,8 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
     // small-world graph the unsettled vertices hang off the settled core
     // by short chains, and a few iterations reach the fixed point that a
     // band per delta would approach in many splits.
-    bool tail = false, tail_next = false;
+    bool tail = false;
+    __shared__ unsigned long long pmin[SSSP_WARPS][32 * PULL_ILP];   // pull pass minima
     // heavy arcs a pull pass would read now, bounded from above: all arcs
     // at first, then what the last pull pass met (the unsettled set only
     // shrinks)
@@ -839,10 +890,12 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             uint32_t *pile = fc ? a.far1 : a.far0;
             t.bandq = pile;
             t.band_count = &ctl->far_count[fc];
-            pull_pass<NARROW>(a, st, T, listed ? pile : nullptr,
+            // with the tail to follow, the pass pushes its first frontier
+            pull_pass<NARROW>(a, st, pmin, T, listed ? pile : nullptr,
                               listed ? min(ldcg_u32(&ctl->far_count[fc]), a.n) : a.n,
-                              listed ? nullptr : pile, &ctl->far_count[fc], attempts, improved,
-                              narrow_miss, atomics);
+                              (listed || a.tail) ? nullptr : pile, &ctl->far_count[fc],
+                              a.tail != 0, t.nbm, t.qn, t.qn_count, t.hqn, t.hqn_count,
+                              attempts, improved, narrow_miss, atomics);
         } else
         for (uint32_t wi = warp; wi < n_work; wi += nwarps) {
             if (wi < n_heavy) {
@@ -996,14 +1049,20 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
             if (first) ctl->exit_reason = 3;
             break;
         }
-        cur_dense = push_dense;
+        // a pull pass that starts the tail set its frontier's bits (dense)
+        cur_dense = (hp && pull && a.tail) ? a.dense != 0 : push_dense;
         ++it;
         const bool was_hp = hp;
         if (hp) {
             ++bands;               // later listings use a fresh tag
             hp = false;
+            if (pull && a.tail) {
+                // the tail band: no threshold, whole rows, no more splits
+                tail = true;
+                T = INF32;
+                if (first) ctl->tail_it = it;
+            }
             if (pull) {
-                tail_next = a.tail != 0;
                 // every thread has read pull_bound at the decision, a
                 // barrier ago; one writes the new bound, read at the next
                 if (threadIdx.x == 0)
@@ -1021,6 +1080,10 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         uint32_t next = ldcg_u32(&ctl->near_count[ns]) + ldcg_u32(&ctl->heavy_count[ns]);
         if (next != 0) continue;
+        if (tail) {                    // the tail's frontier drained: converged
+            if (first) ctl->exit_reason = 1;
+            break;
+        }
         // Band drained: its heavy arcs first (one more iteration), then the
         // split.  The band lists are cleared in the split, so no block can
         // still be reading their counts here.
@@ -1061,12 +1124,6 @@ __global__ void __launch_bounds__(256, 3) sssp_kernel(SsspArgs a) {
         }
         uint64_t T_old = T;
         T = (fmin != INF32 && (uint64_t)fmin > T ? (uint64_t)fmin : T) + a.delta;
-        if (tail_next) {
-            T = INF32;                 // every reached distance is below it
-            tail = true;
-            tail_next = false;
-            if (first) ctl->tail_it = it + 1;
-        }
         ++phase;
         const uint32_t *fs = fc ? a.far1 : a.far0;
         const uint32_t its = it + 1;
