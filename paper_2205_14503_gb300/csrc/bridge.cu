@@ -54,9 +54,8 @@ __device__ __forceinline__ uint64_t scan_label(const ScanArgs &a, uint32_t v) {
 // caller's CSR order whatever the internal vertex order.
 template <bool NARROW>
 __device__ __forceinline__ void scan_arc(const ScanArgs &a, bool valid, uint32_t v, uint64_t lv,
-                                         uint32_t cbase, uint32_t arc, bool &overflow) {
+                                         uint32_t cbase, uint32_t arc, uint2 e, bool &overflow) {
     if (!valid) return;
-    uint2 e = __ldcs(&a.adj[arc]);     // streamed once: evict first
     uint64_t lu = scan_label<NARROW>(a, e.x);
     if (lv == INF64 || lu == INF64) {
         // a reached vertex next to an unreached one: its true distance is
@@ -99,8 +98,14 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
             uint32_t e = min(a.row_ptr[v + 1], s + CHUNK);
             uint64_t lv = scan_label<NARROW>(a, v);
             uint32_t cbase = caller_arc_base(a.orig_of, a.orig_row_ptr, v, rs);
-            for (uint32_t b = s; b < e; b += 32)
-                scan_arc<NARROW>(a, b + lane < e, v, lv, cbase, b + lane, overflow);
+            // the next 32 arcs' records are loaded while these are scanned
+            uint2 en = make_uint2(0, 0);
+            if (s + lane < e) en = __ldcs(&a.adj[s + lane]);    // streamed once: evict first
+            for (uint32_t b = s; b < e; b += 32) {
+                const uint2 ec = en;
+                if (b + 32 + lane < e) en = __ldcs(&a.adj[b + 32 + lane]);
+                scan_arc<NARROW>(a, b + lane < e, v, lv, cbase, b + lane, ec, overflow);
+            }
         } else {
             uint32_t v = (wi - a.n_heavy_chunks) * 32 + lane;
             uint32_t s = 0, deg = 0, cbase = 0;
@@ -115,16 +120,26 @@ __global__ void __launch_bounds__(256) scan_kernel(ScanArgs a) {
             uint32_t incl = warp_inclusive_scan(deg);
             uint32_t excl = incl - deg;
             uint32_t total = __shfl_sync(FULL, incl, 31);
+            // arc j of the batch belongs to the lane whose prefix covers it;
+            // the next 32 arcs' records are loaded while these are scanned
+            uint32_t own = warp_owner_search(excl, lane < total ? lane : 0);
+            const uint32_t s0 = __shfl_sync(FULL, s, own), x0 = __shfl_sync(FULL, excl, own);
+            uint2 en = make_uint2(0, 0);
+            if (lane < total) en = __ldcs(&a.adj[s0 + (lane - x0)]);
             for (uint32_t b = 0; b < total; b += 32) {
-                uint32_t j = b + lane;
-                bool valid = j < total;
-                uint32_t owner = warp_owner_search(excl, valid ? j : 0);
-                uint32_t so = __shfl_sync(FULL, s, owner);
-                uint32_t eo = __shfl_sync(FULL, excl, owner);
-                uint64_t lo = __shfl_sync(FULL, lv, owner);
-                uint32_t co = __shfl_sync(FULL, cbase, owner);
-                uint32_t vo = (wi - a.n_heavy_chunks) * 32 + owner;
-                scan_arc<NARROW>(a, valid, vo, lo, co, so + (j - eo), overflow);
+                const uint32_t j = b + lane;
+                const bool valid = j < total;
+                const uint32_t owner = own;
+                const uint32_t arc = __shfl_sync(FULL, s, owner) + (j - __shfl_sync(FULL, excl, owner));
+                const uint2 ec = en;
+                const uint32_t jn = j + 32;
+                own = warp_owner_search(excl, jn < total ? jn : 0);
+                const uint32_t sn = __shfl_sync(FULL, s, own), xn = __shfl_sync(FULL, excl, own);
+                if (jn < total) en = __ldcs(&a.adj[sn + (jn - xn)]);
+                const uint64_t lo = __shfl_sync(FULL, lv, owner);
+                const uint32_t co = __shfl_sync(FULL, cbase, owner);
+                const uint32_t vo = (wi - a.n_heavy_chunks) * 32 + owner;
+                scan_arc<NARROW>(a, valid, vo, lo, co, arc, ec, overflow);
             }
         }
     }
