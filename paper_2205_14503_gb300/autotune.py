@@ -14,7 +14,9 @@ library's own CUDA events; at the best point it then tries the label width
 (32-bit labels halve the random label traffic of scale-free graphs but add
 work to the latency-bound hops of a grid) and how a band split finds the
 vertices left for later bands (a pile of far proposals or a scan of every
-label).  It applies the fastest and caches it in a JSON file keyed by a
+label), and whether the rest of the phase after a pull-form heavy pass
+runs as one unbounded band (the tail) or keeps its bands.  It applies the
+fastest and caches it in a JSON file keyed by a
 fingerprint of the graph and the GPU name, so later handles of the same
 graph start tuned (``apply_cached``).  Results never depend on these
 settings, only the time does.  Tune on sample queries other than the ones
