@@ -647,8 +647,9 @@ def run_ablation_mode(args, world, rank, local):
     """Relaxation order (the paper's priority-ordered messages against a
     plain frontier): per single-query workload, the Voronoi phase as a
     Bellman-Ford frontier (one unbounded band), as near/far bands at the
-    tuned width, and with the tuned block-local rounds; time, relaxations
-    per arc and iterations of each."""
+    tuned width with the heavy arcs pushed, pushed or pulled, and pulled
+    then followed by the unbounded tail, and with the tuned block-local
+    rounds; time, relaxations per arc and iterations of each."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -665,15 +666,21 @@ def run_ablation_mode(args, world, rank, local):
         seeds = wl.config_seed_sets(cfg, g)[0]
         with st.SteinerGraph(g, device=local) as G:
             tuned = autotune.tune(G, g, [seeds], cache_path=None, device=local)
-            variants = [("frontier (Bellman-Ford)", 0x7FFFFFFF, 0),
-                        ("near/far", tuned["delta"], 0),
-                        ("near/far + block-local rounds", tuned["delta"], tuned["local_rounds"])]
+            d, lr_t = tuned["delta"], tuned["local_rounds"]
+            # (name, delta, local rounds, heavy-pass form, unbounded tail)
+            variants = [("frontier (Bellman-Ford)", 0x7FFFFFFF, 0, 1, 1),
+                        ("near/far, heavy arcs pushed", d, 0, 0, 0),
+                        ("near/far, heavy arcs pushed or pulled", d, 0, 1, 0),
+                        ("near/far, pulled, then unbounded tail", d, 0, 1, 1),
+                        ("near/far + block-local rounds", d, lr_t, 1, tuned.get("tail", 1))]
             ref = None
-            for name, delta, lr in variants:
+            for name, delta, lr, pull, tail in variants:
                 if name.endswith("rounds") and lr == 0:
                     continue
                 G.set_param("delta", delta)
                 G.set_param("local_rounds", lr)
+                G.set_param("pull", pull)
+                G.set_param("tail", tail)
                 G.query_detail(seeds, pairs=False)
                 ms, att, its = [], [], []
                 for _ in range(max(1, args.steps)):
@@ -685,6 +692,7 @@ def run_ablation_mode(args, world, rank, local):
                     ref = r.total
                 assert r.total == ref, "schedules must reach the same tree"
                 rows.append({"workload": g.name, "order": name, "delta": delta, "local_rounds": lr,
+                             "pull": pull, "tail": tail,
                              "ms_voronoi": statistics.median(ms),
                              "relaxations_per_arc": statistics.mean(att) / g.n_arcs,
                              "iterations": statistics.mean(its), "total": int(r.total)})
