@@ -553,6 +553,7 @@ def run_batch_mode(args, world, rank, local):
                                                             "label_bits", "far_scan")}
                        if tuned else None},
             "batch_delta": (btuned or {}).get("batch_delta"),
+            "batch_pull": (btuned or {}).get("batch_pull"),
             "plain_queries_per_s": nq / t_plain, "speedup_vs_plain": t_plain / t_batch,
             "identical_to_plain": same, "phase_ms": parts}
     print(json.dumps(line), flush=True)
@@ -630,6 +631,7 @@ def run_serve_mode(args, world, rank, local):
                        "k_range": [3, 10000], "budget_bytes": 40 << 30, "slots": 64,
                        "yield_div": G_yield_div,
                        "batch_delta": (btuned or {}).get("batch_delta"),
+            "batch_pull": (btuned or {}).get("batch_pull"),
                        "tuned": {k: tuned.get(k) for k in ("delta", "sssp_blocks", "local_rounds",
                                                             "label_bits", "far_scan")}
                        if tuned else None},

@@ -207,6 +207,11 @@ int steiner_serve_stop(steiner_graph_t g);
  *                  just queued, a hop per round, before the grid barrier
  *   "batch_delta"  band width of the multi-query engine (0 = w_max / 8 when
  *                  "delta" is at most the largest weight w_max, else "delta")
+ *   "batch_pull"   1 (default): a query's first heavy-arc pass in the
+ *                  multi-query engine runs in the pull form (each vertex
+ *                  unsettled in that query reads its own heavy arcs and the
+ *                  labels at their other ends); 0: it pushes the heavy arcs
+ *                  of the band's vertices
  *   "batch_tails"  1 (default): the tails (MST, expansion, sorted edges) of
  *                  the queries that finish together run as one launch per
  *                  step for all of them; 0: one query at a time
@@ -249,7 +254,8 @@ int steiner_serve_stop(steiner_graph_t g);
  * "batch_pairs", "batch_t0".."batch_t4" in nanoseconds, "batch_admitted"
  * (queries admitted into slots), "batch_admitted_busy" (of those, the
  * ones admitted while other slots were still on the device) and
- * "batch_tail_batches" (retirements whose tails ran batched) and
+ * "batch_tail_batches" (retirements whose tails ran batched),
+ * "batch_pull_sweeps" (pull-form passes the engine ran) and
  * "batch_narrow_reruns" (queries answered by the single-query path because
  * a distance outgrew the engine's 32-bit labels); "batch_reset" clears the
  * timers).  It returns -1 for an unknown key.

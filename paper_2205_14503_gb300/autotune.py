@@ -175,13 +175,15 @@ def tune_batch(G: "st.SteinerGraph", graph, sample_queries,
                width_factors=(1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2), reps: int = 2) -> dict:
     """Band width of the multi-query engine: times whole batched runs
     (steiner_query_batch, wall clock) of the sample queries at band widths
-    spread over the weight range and at the single-query delta, and applies
-    the fastest.  Run ``tune`` first (the single-query delta is one of the
+    spread over the weight range and at the single-query delta, applies the
+    fastest, then times the push form of each slot's first heavy-arc pass
+    there against the pull form and keeps the faster.  Run ``tune`` first (the single-query delta is one of the
     candidates) and use sample queries other than the ones to be timed."""
     import time
     wmax = int(np.max(graph.w)) if graph.n_arcs else 1
     cands = sorted({max(1, int(round(wmax * f))) for f in width_factors}
                    | {int(G.get_param("delta"))})
+    G.set_param("batch_pull", 1)
     trials = []
     for d in cands:
         G.set_param("batch_delta", d)
@@ -195,5 +197,17 @@ def tune_batch(G: "st.SteinerGraph", graph, sample_queries,
     trials.sort()
     best_ms, d = trials[0]
     G.set_param("batch_delta", d)
-    return {"batch_delta": d, "ms_batch": best_ms,
-            "trials": [{"ms": t, "batch_delta": x} for t, x in trials]}
+    # every trial so far ran each slot's first heavy-arc pass in the pull
+    # form; the push form at the chosen width
+    G.set_param("batch_pull", 0)
+    G.query_batch(sample_queries)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc, res = G.query_batch(sample_queries)
+        if rc not in (st.STEINER_OK, st.STEINER_EDISCONNECTED):
+            raise st.SteinerError(rc, st.last_error())
+    push_ms = 1e3 * (time.perf_counter() - t0) / reps
+    pull = 0 if push_ms < best_ms else 1
+    G.set_param("batch_pull", pull)
+    return {"batch_delta": d, "batch_pull": pull, "ms_batch": min(best_ms, push_ms),
+            "ms_push": push_ms, "trials": [{"ms": t, "batch_delta": x} for t, x in trials]}

@@ -58,6 +58,7 @@ struct MqArgs {
     // with the split: end of each row's light part in the weight-partitioned
     // adjacency `adj` (null: rows are unpartitioned and arcs are filtered)
     const uint32_t *lend;
+    uint32_t pull;           // first heavy-arc pass of a slot in the pull form
 };
 
 __device__ __forceinline__ uint32_t *band_list(const MqArgs &a, uint32_t i) {
@@ -280,6 +281,121 @@ __device__ __forceinline__ void mq_relax(const MqArgs &a, MqStage &st, const MqT
     }
 }
 
+// Pull form of the first heavy-arc pass of the slots in P.  A slot in its
+// first band has threshold delta; once its near work drained, every label
+// below it is final, and a heavy arc (weight delta or more) brings a vertex
+// still at or above it only a proposal at or above it.  So instead of
+// pushing the heavy arcs of the band's vertices, every vertex unsettled in
+// some slot of P reads its own heavy arcs and, per arc, the label run of the
+// other end.  Warps sweep the vertices one at a time, lane l serving slots
+// l and l + 32; each lane keeps its slots' best proposal from settled ends
+// in registers and, after the row, sends one atomicMin per improved
+// (vertex, slot) and does the bookkeeping of mq_relax for it (a far
+// proposal: far mask, far pending count, far minimum, far pile).  Only
+// this warp writes these labels during the iteration: the band items of
+// the iteration leave out the slots of P, and those slots have no near
+// work.
+__device__ __noinline__ void mq_pull_sweep(const MqArgs &a, MqStage &st, unsigned long long P,
+                                           uint32_t *qn, uint32_t *qn_count, uint32_t *farq,
+                                           uint32_t *far_count, uint32_t tag_next,
+                                           unsigned long long &attempts,
+                                           unsigned long long &improved,
+                                           unsigned long long &narrow_miss) {
+    MqTargets t;
+    t.qn = qn;
+    t.qn_count = qn_count;
+    t.act = nullptr;
+    t.farq = farq;
+    t.far_count = far_count;
+    t.fmin = nullptr;
+    t.tag_next = tag_next;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t q0 = lane, q1 = lane + 32;
+    const bool p0 = (P >> q0) & 1ull, p1 = (P >> q1) & 1ull;
+    const uint32_t sh0 = st.lshift[q0], sh1 = st.lshift[q1];
+    const unsigned long long T0 = st.T[q0], T1 = st.T[q1];
+    const uint64_t lm0 = (1ull << (32 - sh0)) - 2, lm1 = (1ull << (32 - sh1)) - 2;
+    for (uint32_t v = warp; v < a.n; v += nwarps) {
+        const uint64_t base = (uint64_t)v * MQ_SLOTS;
+        const uint64_t la = p0 ? widen_label(ldcg_u32(&a.label[base + q0]), sh0) : 0ull;
+        const uint64_t lb = p1 ? widen_label(ldcg_u32(&a.label[base + q1]), sh1) : 0ull;
+        const bool ua = p0 && (la == INF64 || (la >> 32) >= T0);
+        const bool ub = p1 && (lb == INF64 || (lb >> 32) >= T1);
+        if (!__any_sync(FULL, ua || ub)) continue;
+        const uint32_t r1 = a.row_ptr[v + 1];
+        const uint32_t s = a.lend ? a.lend[v] : a.row_ptr[v];
+        uint64_t ba = INF64, bb = INF64;
+        for (uint32_t j = s; j < r1; ++j) {
+            const uint2 e = a.adj[j];                  // one record, every lane
+            if (e.y < a.delta) continue;               // light (unpartitioned rows only)
+            const uint64_t ub_ = (uint64_t)e.x * MQ_SLOTS;
+            const uint32_t xa = ua ? ldcg_u32(&a.label[ub_ + q0]) : INF32;
+            const uint32_t xb = ub ? ldcg_u32(&a.label[ub_ + q1]) : INF32;
+            if (xa != INF32) {
+                const uint64_t lu = widen_label(xa, sh0);
+                if ((lu >> 32) < T0) {                 // a settled end proposes
+                    ++attempts;
+                    const uint64_t nd = (lu >> 32) + (uint64_t)e.y;
+                    if (nd > lm0) {
+                        if (la == INF64) narrow_miss |= 1ull << q0;
+                    } else {
+                        ba = min(ba, (uint64_t)((nd << 32) | (lu & 0xFFFFFFFFull)));
+                    }
+                }
+            }
+            if (xb != INF32) {
+                const uint64_t lu = widen_label(xb, sh1);
+                if ((lu >> 32) < T1) {
+                    ++attempts;
+                    const uint64_t nd = (lu >> 32) + (uint64_t)e.y;
+                    if (nd > lm1) {
+                        if (lb == INF64) narrow_miss |= 1ull << q1;
+                    } else {
+                        bb = min(bb, (uint64_t)((nd << 32) | (lu & 0xFFFFFFFFull)));
+                    }
+                }
+            }
+        }
+        const bool ia = ua && ba < la, ib = ub && bb < lb;
+        if (ia) atomicMin(&a.label[base + q0], ((uint32_t)(ba >> 32) << sh0) | (uint32_t)ba);
+        if (ib) atomicMin(&a.label[base + q1], ((uint32_t)(bb >> 32) << sh1) | (uint32_t)bb);
+        const bool fa = ia && (ba >> 32) >= T0, fb = ib && (bb >> 32) >= T1;
+        unsigned long long nbits = (ia && !fa ? 1ull << q0 : 0ull) | (ib && !fb ? 1ull << q1 : 0ull);
+        unsigned long long fbits = (fa ? 1ull << q0 : 0ull) | (fb ? 1ull << q1 : 0ull);
+        nbits = warp_or64(nbits);
+        fbits = warp_or64(fbits);
+        if (!(nbits | fbits)) continue;
+        improved += (ia ? 1u : 0u) + (ib ? 1u : 0u);
+        unsigned long long fold = 0;
+        bool to_far = false, to_near = false;
+        if (lane == 0) {
+            if (fbits) {
+                fold = atomicOr(&a.fmask[v], fbits);
+                to_far = atomicExch(&a.in_far[v], 1u) == 0;
+            }
+            if (nbits) {
+                atomicOr(&a.nmask[v], nbits);
+                to_near = atomicExch(&a.stamp_near[v], tag_next) != tag_next;
+                atomicOr(&st.act, nbits);
+            }
+        }
+        fold = __shfl_sync(FULL, fold, 0);
+        if (fa) {
+            if (!((fold >> q0) & 1ull)) atomicAdd(&st.fpend[q0], 1);
+            atomicMin(&st.fmin[q0], (uint32_t)(ba >> 32));
+        }
+        if (fb) {
+            if (!((fold >> q1) & 1ull)) atomicAdd(&st.fpend[q1], 1);
+            atomicMin(&st.fmin[q1], (uint32_t)(bb >> 32));
+        }
+        mq_push_near(a, st, t, to_near, v);
+        stage_append(to_far, v, st.far_buf, &st.far_n, MQ_FAR_STAGE, t.farq, t.far_count, a.n,
+                     &a.ctl->err);
+    }
+}
+
 __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
     __shared__ MqStage st;
     MqControl *ctl = a.ctl;
@@ -295,6 +411,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
     // heavy-arc passes: H = slots whose pass runs in this iteration
     unsigned long long H = __ldcg(&ctl->hpass) & infl;
     unsigned long long hp_done = __ldcg(&ctl->hp_done);
+    unsigned long long band0 = __ldcg(&ctl->band0);
+    uint32_t pull_sweeps = 0;
     uint32_t bc = ldcg_u32(&ctl->blist);
     if (threadIdx.x < MQ_SLOTS) {
         st.T[threadIdx.x] = __ldcg(&ctl->T[threadIdx.x]);
@@ -315,6 +433,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
         // heavy-arc pass) the band list.  A pass reads list bc and moves the
         // survivors, with this iteration's new listings, to list bc + 1;
         // list bc + 2 (read by the previous pass) is cleared for the next.
+        // slots of H in their first band run the pass in the pull form
+        const unsigned long long P = a.pull ? (H & band0) : 0ull;
         const uint32_t n_band = H ? min(ldcg_u32(&ctl->bcount[bc]), a.n) : 0u;
         const uint32_t n_all = n_items + n_band;
         const uint32_t tgt = H ? (bc + 1) % 3 : bc;
@@ -352,7 +472,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                 } else {
                     u = ldcg_u32(&blo[i - n_items]);
                     const unsigned long long old = atomicAnd(&a.bmask[u], ~H);
-                    M = old & H;                 // the slots whose band closes now
+                    M = old & H & ~P;            // the slots whose band closes now (pushed)
                     listed = (old & ~H) != 0ull; // still in other slots' bands
                 }
                 a.item_mask[i] = M;
@@ -523,6 +643,11 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
                 i0 += 32;
             }
         }
+        if (P) {
+            mq_pull_sweep(a, st, P, t.qn, t.qn_count, t.farq, t.far_count, t.tag_next, attempts,
+                          improved, narrow_miss);
+            ++pull_sweeps;
+        }
         unsigned long long tm3 = first ? gtimer() : 0;
         seg_flush(st, t, ctl, a.n);
         if (first)
@@ -556,6 +681,7 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
             else S |= 1ull << q;
         }
         hp_done &= ~S;                      // a split opens a new band
+        band0 &= ~S;
         infl &= ~conv;
         conv_total |= conv;
         if (!infl) { reason = 1; break; }
@@ -662,6 +788,8 @@ __global__ void __launch_bounds__(256, 6) mq_sssp_kernel(MqArgs a) {
         ctl->fc = fc;
         ctl->hpass = H & infl;
         ctl->hp_done = hp_done;
+        ctl->band0 = band0;
+        ctl->pull_sweeps += pull_sweeps;
         ctl->blist = bc;
         ctl->converged |= conv_total;
         ctl->iterations = iters;
@@ -716,6 +844,7 @@ __global__ void mq_seed_kernel(const uint32_t *__restrict__ row_ptr, uint32_t n,
         ctl->slot_overflow &= ~bit;
         ctl->hp_done &= ~bit;
         ctl->hpass &= ~bit;
+        ctl->band0 |= bit;
     }
     if (r >= k) return;
     uint32_t s = internal_id(new_of, (uint32_t)seeds[r]);
@@ -1024,7 +1153,7 @@ cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uin
     return cudaGetLastError();
 }
 
-cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
+cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta, uint32_t pull,
                            uint32_t max_iters, uint32_t yield, const uint32_t *doorbell,
                            cudaStream_t s) {
     MqArgs a;
@@ -1050,6 +1179,7 @@ cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t d
     a.defer = delta <= g.max_w ? 1u : 0u;
     a.lend = active_lend(g, delta);
     if (a.lend) a.adj = g.adj_w;        // rows partitioned by weight class
+    a.pull = a.defer ? pull : 0u;
     a.ctl = m.ctl;
     a.doorbell = doorbell;
     a.delta = delta;

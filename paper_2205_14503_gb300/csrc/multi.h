@@ -53,6 +53,10 @@ struct MqControl {
     uint32_t bcount[3];
     uint32_t lshift[MQ_SLOTS];          // rank bits of each slot's 32-bit labels
     unsigned long long slot_narrow;     // slots with a distance too large for their labels
+    // slots still in their first band (set at admission, cleared by the
+    // slot's first split): their heavy-arc pass may run in the pull form
+    unsigned long long band0;
+    uint32_t pull_sweeps;               // pull-form passes run (accumulated)
 };
 
 struct MqState {
@@ -141,7 +145,7 @@ cudaError_t mq_launch_seed(const DevGraph &g, MqState &m, int q, uint32_t k, uin
 // Runs the persistent multi-query SSSP.  yield > 0: return once `yield`
 // slots converged or *doorbell (host-mapped) is set; yield = 0: run until
 // every in-flight slot converged.  max_iters caps this launch.
-cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta,
+cudaError_t mq_launch_sssp(const DevGraph &g, MqState &m, int blocks, uint32_t delta, uint32_t pull,
                            uint32_t max_iters, uint32_t yield, const uint32_t *doorbell,
                            cudaStream_t s);
 // Clears the shared frontier state (after an error).

@@ -61,6 +61,9 @@ struct BatchEngine {
     // Band width of every slot's near/far threshold (0 = the graph's
     // single-query default).
     uint32_t batch_delta = 0;
+    // 1: each slot's first heavy-arc pass runs in the pull form (unsettled
+    // vertices read their heavy arcs); 0: every pass pushes
+    uint32_t pull = 1;
     // A yielding launch returns once popc(in flight) / yield_div slots
     // converged (at least one), or when the doorbell rings (a request waits
     // and a slot is free).  1 (the default) retires whole waves: slots that
@@ -248,7 +251,7 @@ struct BatchEngine {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&m.ctl->converged, &h_masks[1], 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = mq_launch_sssp(api_graph(G), m, blocks, delta, 1u << 20,
+            e = mq_launch_sssp(api_graph(G), m, blocks, delta, pull, 1u << 20,
                                yield ? std::max(1u, (uint32_t)__builtin_popcountll(inflight) / yield_div) : 0u,
                                doorbell_dev, s);
         if (e == cudaSuccess)
@@ -384,6 +387,8 @@ int64_t batch_counter(BatchEngine *B, const char *key) {
     if (k == "batch_admitted") return (int64_t)B->admitted;
     if (k == "batch_admitted_busy") return (int64_t)B->admitted_busy;
     if (k == "batch_tails") return B->batched_tails;
+    if (k == "batch_pull") return B->pull;
+    if (k == "batch_pull_sweeps" && B->h_ctl) return (int64_t)B->h_ctl->pull_sweeps;
     if (k == "batch_tail_batches") return (int64_t)B->tail_batches;
     if (k == "batch_narrow_reruns") return (int64_t)B->narrow_reruns;
     if (k == "batch_delta") return B->cur_delta();
@@ -409,7 +414,8 @@ static BatchEngine *engine_of(steiner_graph *G) {
     return B;
 }
 
-// Engine settings (steiner_set_param keys "batch_delta", "batch_yield_div").
+// Engine settings (steiner_set_param keys "batch_delta", "batch_pull", "batch_tails",
+// "batch_yield_div").
 int batch_set_param(steiner_graph *G, const char *key, int64_t value) {
     BatchEngine *B = engine_of(G);
     std::string k(key);
@@ -419,6 +425,14 @@ int batch_set_param(steiner_graph *G, const char *key, int64_t value) {
             return STEINER_EINVAL;
         }
         B->batch_delta = (uint32_t)value;
+        return STEINER_OK;
+    }
+    if (k == "batch_pull") {
+        if (value != 0 && value != 1) {
+            api_set_error("batch_pull must be 0 or 1");
+            return STEINER_EINVAL;
+        }
+        B->pull = (uint32_t)value;
         return STEINER_OK;
     }
     if (k == "batch_tails") {

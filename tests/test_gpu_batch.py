@@ -202,19 +202,26 @@ def test_serving_budget_refusals():
     assert got[t_ok][0] == st.STEINER_OK
 
 
+@pytest.mark.parametrize("pull", [0, 1])
 @pytest.mark.parametrize("batch_delta", [1, 100, 999])
-def test_batch_light_heavy_split(batch_delta):
+def test_batch_light_heavy_split(batch_delta, pull):
     """Band widths at or below the largest weight switch on the per-slot
     light/heavy arc split of the batched kernel (heavy-arc passes of
-    different slots interleaved with other slots' bands); trees equal the
-    oracle's on a grid and on an R-MAT graph with hubs."""
+    different slots interleaved with other slots' bands); a slot's first
+    heavy-arc pass pushes the band's heavy arcs (pull 0) or lets every
+    vertex unsettled in that slot read its own (pull 1), while other slots
+    push or relax in the same iterations.  Trees equal the oracle's on a
+    grid and on an R-MAT graph with hubs."""
     for g, grid in ((wl.grid(160, 120, 1000, seed=47), True), (wl.rmat(12, 48, wmax=1000, seed=48), False)):
         pool = np.arange(g.n, dtype=np.int32) if grid else wl.largest_cc(g)
         qs = _queries(pool, [2, 9, 40, 3, 120, 17, 64, 5], 6 + batch_delta)
         with st.SteinerGraph(g) as Gd:
             Gd.set_param("batch_delta", batch_delta)
+            Gd.set_param("batch_pull", pull)
             rc, res = Gd.query_batch(qs)
+            sweeps = Gd.get_param("batch_pull_sweeps")
         assert rc == st.STEINER_OK
+        assert (sweeps > 0) == bool(pull)
         _check(g, qs, res)
 
 
