@@ -177,8 +177,9 @@ def tune_batch(G: "st.SteinerGraph", graph, sample_queries,
     (steiner_query_batch, wall clock) of the sample queries at band widths
     spread over the weight range and at the single-query delta, applies the
     fastest, then times the push form of each slot's first heavy-arc pass
-    there against the pull form and keeps the faster.  Run ``tune`` first (the single-query delta is one of the
-    candidates) and use sample queries other than the ones to be timed."""
+    there against the pull form and keeps the faster.  Run ``tune`` first
+    (the single-query delta is one of the candidates) and use sample
+    queries other than the ones to be timed."""
     import time
     wmax = int(np.max(graph.w)) if graph.n_arcs else 1
     cands = sorted({max(1, int(round(wmax * f))) for f in width_factors}

@@ -79,3 +79,44 @@ def test_apply_cached_restores_every_choice(tmp_path, monkeypatch):
     assert got["delta"] == e["delta"] == 250
     for key in ("delta", "sssp_blocks", "local_rounds", "label_bits", "far_scan", "tail"):
         assert H.p[key] == e[key]
+
+
+class FakeBatchHandle(FakeHandle):
+    """query_batch advances a fake wall clock by `bcost(params)` ms."""
+
+    def __init__(self, bcost, clock, **kw):
+        super().__init__(lambda p: 0.0, **kw)
+        self.p.update({"batch_delta": 0, "batch_pull": 1})
+        self.bcost = bcost
+        self.clock = clock
+
+    def query_batch(self, queries):
+        self.clock[0] += self.bcost(self.p) / 1e3
+        return st.STEINER_OK, []
+
+
+def _fake_clock(monkeypatch):
+    import time
+    clock = [0.0]
+    monkeypatch.setattr(time, "perf_counter", lambda: clock[0])
+    return clock
+
+
+def test_tune_batch_picks_width_then_push_or_pull(monkeypatch):
+    clock = _fake_clock(monkeypatch)
+    g = _graph()
+    g.w = np.array([1000, 1000, 7, 7], np.uint32)        # w_max 1000: widths 31 .. 500
+
+    def bcost(p):
+        return abs(np.log(p["batch_delta"] / 250.0)) * 10 + (3.0 if p["batch_pull"] else 1.0)
+
+    G = FakeBatchHandle(bcost, clock, delta0=45)
+    e = autotune.tune_batch(G, g, [np.array([0, 2], np.int32)], reps=1)
+    assert (e["batch_delta"], e["batch_pull"]) == (250, 0)       # push measured faster here
+    assert (G.p["batch_delta"], G.p["batch_pull"]) == (250, 0)
+    assert abs(e["ms_push"] - 1.0) < 1e-6
+
+    G = FakeBatchHandle(lambda p: abs(np.log(p["batch_delta"] / 125.0)) * 10 +
+                        (1.0 if p["batch_pull"] else 3.0), clock, delta0=45)
+    e = autotune.tune_batch(G, g, [np.array([0, 2], np.int32)], reps=1)
+    assert (e["batch_delta"], e["batch_pull"]) == (125, 1)
